@@ -1,0 +1,178 @@
+"""Domain decomposition index maps (Sec. 3.2.1 and the permutation paragraph of Sec. 3.2.2; Sec. 4).
+
+Readings fixed where the paper is silent (listed in the design doc):
+
+* Contact interfaces (Sec. 3.2.2, "thinnest 4-/6-connected collection of pixels that separate two
+  primary grids"): a void cell of label a is an interface cell when a face-neighbour (wrapping along
+  periodic axes) is void with a label b > a; its pair is (a, smallest such b).  Interfaces are the
+  face-connected components of interface cells sharing a pair, numbered by their lowest cell index.
+* Primary grid of label a = its cells that are not interface cells; labels that keep at least one
+  cell are numbered in ascending label order (others are dropped and counted).
+* Faces (Sec. 3.2.2): a face unknown with at least one flanking cell in primary grid i belongs to i
+  (two different primary grids never flank one face); a face flanked by two interface cells is an
+  interface face ("f").
+* C^{p_i} = interfaces owning a cell face-adjacent to a cell of p_i (sorted ascending).
+* Dual grid j (Sec. 3.2.1): cells of interface j dilated `n_dilate` times over face-neighbouring void
+  cells; its unknowns are those cells and every face unknown with a flanking cell among them.
+* gPLMM tags (Sec. 4, "faces within a few layers of each contact interface", 3-point stencil):
+  every f face, plus every primary face whose same-component neighbour along some axis is an unknown
+  outside its own primary grid; `n_tag` > 1 adds faces adjacent (same rule) to tagged faces.
+"""
+from __future__ import annotations
+
+from collections import deque
+
+import numpy as np
+
+F_FACE = -1        # face class of interface (f) faces
+NOT_UNKNOWN = -2
+
+
+class Maps:
+    pass
+
+
+def build_maps(g, labels, pins, n_dilate=2, n_tag=1):
+    L = np.asarray(labels).ravel().astype(np.int64)
+    if np.any(L[g.void] < 1) or np.any(L[~g.void] != 0):
+        raise ValueError("labels must be >= 1 on void cells and 0 on solid cells")
+    m = Maps()
+    m.pins = np.asarray(pins)
+    # --- interface cells and their pairs
+    big = np.iinfo(np.int64).max
+    partner = np.full(g.ncell, big)
+    for a in range(g.dim):
+        for t in (0, 1):
+            n = g.nb[a][t]
+            ok = g.void & (n >= 0)
+            ns = np.where(ok, n, 0)
+            ok &= g.void[ns]
+            cand = np.where(ok & (L[ns] > L), L[ns], big)
+            partner = np.minimum(partner, cand)
+    is_if = g.void & (partner < big)
+    # --- interfaces: components of same-pair interface cells
+    iface = np.full(g.ncell, -1, np.int64)
+    n_if = 0
+    for s in np.flatnonzero(is_if):
+        if iface[s] >= 0:
+            continue
+        key = (L[s], partner[s])
+        iface[s] = n_if
+        q = deque([s])
+        while q:
+            c = q.popleft()
+            for a in range(g.dim):
+                for t in (0, 1):
+                    n = g.nb[a][t][c]
+                    if n >= 0 and is_if[n] and iface[n] < 0 and (L[n], partner[n]) == key:
+                        iface[n] = n_if
+                        q.append(n)
+        n_if += 1
+    m.n_iface = n_if
+    m.cell_iface = iface
+    m.iface_pair = np.zeros((n_if, 2), np.int64)
+    for j in range(n_if):
+        c = np.flatnonzero(iface == j)[0]
+        m.iface_pair[j] = (L[c], partner[c])
+    m.iface_cells = [np.flatnonzero(iface == j) for j in range(n_if)]
+    # --- primary grids
+    prim_cells = g.void & ~is_if
+    labs = np.unique(L[prim_cells])
+    all_labs = np.unique(L[g.void])
+    m.dropped_labels = np.setdiff1d(all_labs, labs)
+    lab2p = {int(v): i for i, v in enumerate(labs)}
+    cell_prim = np.full(g.ncell, -1, np.int64)
+    for c in np.flatnonzero(prim_cells):
+        cell_prim[c] = lab2p[int(L[c])]
+    m.n_prim = len(labs)
+    m.cell_prim = cell_prim
+    # --- face classes
+    m.face_class = []
+    for d in range(g.dim):
+        lo = g.nb[d][0]
+        los = np.where(lo >= 0, lo, 0)
+        pl = np.where(lo >= 0, cell_prim[los], -1)
+        ph = cell_prim
+        clash = g.face_unknown[d] & (pl >= 0) & (ph >= 0) & (pl != ph)
+        if np.any(clash):
+            raise RuntimeError("a face is flanked by two different primary grids")
+        cls = np.where(ph >= 0, ph, np.where(pl >= 0, pl, F_FACE))
+        m.face_class.append(np.where(g.face_unknown[d], cls, NOT_UNKNOWN))
+    # --- C^{p_i}
+    cp = [set() for _ in range(m.n_prim)]
+    for c in np.flatnonzero(is_if):
+        for a in range(g.dim):
+            for t in (0, 1):
+                n = g.nb[a][t][c]
+                if n >= 0 and cell_prim[n] >= 0:
+                    cp[cell_prim[n]].add(int(iface[c]))
+    m.C = [np.array(sorted(s), np.int64) for s in cp]
+    # --- unknown lists (global indices, ascending: faces by axis, then cells)
+    m.prim_unknowns = []
+    for i in range(m.n_prim):
+        parts = [g.fidx(d, np.flatnonzero(m.face_class[d] == i)) for d in range(g.dim)]
+        parts.append(g.pidx(np.flatnonzero(cell_prim == i)))
+        m.prim_unknowns.append(np.concatenate(parts))
+    m.f_faces = np.concatenate([g.fidx(d, np.flatnonzero(m.face_class[d] == F_FACE)) for d in range(g.dim)])
+    # --- dual grids
+    m.dual_unknowns = []
+    m.dual_cells = []
+    for j in range(n_if):
+        inset = np.zeros(g.ncell, bool)
+        inset[m.iface_cells[j]] = True
+        for _ in range(n_dilate):
+            grow = inset.copy()
+            for a in range(g.dim):
+                for t in (0, 1):
+                    n = g.nb[a][t]
+                    ok = inset & (n >= 0)
+                    tgt = n[ok]
+                    tgt = tgt[g.void[tgt]]
+                    grow[tgt] = True
+            inset = grow
+        parts = []
+        for d in range(g.dim):
+            lo = g.nb[d][0]
+            los = np.where(lo >= 0, lo, 0)
+            sel = g.face_unknown[d] & (inset | ((lo >= 0) & inset[los]))
+            parts.append(g.fidx(d, np.flatnonzero(sel)))
+        parts.append(g.pidx(np.flatnonzero(inset)))
+        m.dual_unknowns.append(np.concatenate(parts))
+        m.dual_cells.append(np.flatnonzero(inset))
+    # --- gPLMM tags
+    tags = [np.zeros(g.ncell, bool) for _ in range(g.dim)]
+    for d in range(g.dim):
+        cls = m.face_class[d]
+        tags[d] |= cls == F_FACE
+        for a in range(g.dim):
+            for t in (0, 1):
+                ix, ok = g.face_at(d, g.nb[a][t])
+                other = ok & (m.face_class[d][ix] != cls)
+                tags[d] |= (cls >= 0) & other
+    for _ in range(n_tag - 1):
+        new = [t.copy() for t in tags]
+        for d in range(g.dim):
+            cls = m.face_class[d]
+            for a in range(g.dim):
+                for t in (0, 1):
+                    ix, ok = g.face_at(d, g.nb[a][t])
+                    new[d] |= (cls >= 0) & ok & tags[d][ix]
+        tags = new
+    m.tags = tags
+    # --- owner of every global unknown: primary id, -1 interface cell, -3 f face, -2 not unknown
+    owner = np.full(g.nfull, NOT_UNKNOWN, np.int64)
+    for d in range(g.dim):
+        cls = m.face_class[d]
+        owner[g.fidx(d, np.arange(g.ncell))] = np.where(cls == F_FACE, -3, cls)
+    cellown = np.where(cell_prim >= 0, cell_prim, np.where(iface >= 0, -1, NOT_UNKNOWN))
+    owner[g.pidx(np.arange(g.ncell))] = cellown
+    m.owner = owner
+    return m
+
+
+def dual_fraction(g, m):
+    """Fraction f^d of unknowns covered by at least one dual grid (Sec. 7 cost model: 10-30%)."""
+    cov = np.zeros(g.nfull, bool)
+    for u in m.dual_unknowns:
+        cov[u] = True
+    return cov.sum() / len(g.unknown)

@@ -1,0 +1,409 @@
+"""Seeded synthetic porous images, pore labels and Reynolds-number helpers.
+
+This module makes the inputs of the solver and nothing else: binary void masks shaped like the paper's
+porous samples (disk packs as in PD4/GLD4, sphere packs as in Granular, a thresholded Gaussian random
+field as a stand-in for a sandstone), a watershed labelling of the void into pores (the primary-grid
+decomposition of Sec. 3.2.1 takes these labels as given), and the Reynolds-number definition of
+Sec. 6 (Re = rho U l / mu with U = U_D / phi and l = V_s / A_w).  It holds none of the solver's
+arithmetic: no discretisation, no preconditioner, no Krylov step.
+
+Image convention: arrays of shape (nz, ny, nx), C order, x fastest; a 2D image has nz == 1.
+mask == 1 marks void (fluid) cells.  Axis 0 of the solver is x, axis 1 is y, axis 2 is z.
+`periodic` is a tuple of three booleans (x, y, z); the default workloads are periodic in x only.
+"""
+from __future__ import annotations
+
+import heapq
+from dataclasses import dataclass
+
+import numpy as np
+from scipy import ndimage
+
+X_PERIODIC = (True, False, False)
+
+
+# ----------------------------------------------------------------------------------------------
+# geometry generators
+# ----------------------------------------------------------------------------------------------
+def _wrap_delta(a, b, n):
+    """Signed distance a - b on a ring of length n (minimum image)."""
+    d = (a - b) % n
+    return np.where(d > n / 2, d - n, d)
+
+
+def disk_pack_2d(n: int = 64, n_disks: int = 12, rmin: float = 4.0, rmax: float = 8.0, seed: int = 0,
+                 max_tries: int = 200000) -> np.ndarray:
+    """Non-overlapping disks with radius U[rmin, rmax] and uniform centres, x-periodic, clipped at the
+    y walls (rejection sampling).  Returns the void mask, shape (1, n, n), uint8."""
+    rng = np.random.default_rng(seed)
+    disks = []
+    tries = 0
+    while len(disks) < n_disks:
+        tries += 1
+        if tries > max_tries:
+            raise RuntimeError("disk packing did not finish; lower n_disks or radii")
+        r = rng.uniform(rmin, rmax)
+        cx, cy = rng.uniform(0, n), rng.uniform(0, n)
+        ok = True
+        for (qx, qy, qr) in disks:
+            dx = _wrap_delta(cx, qx, n)
+            if dx * dx + (cy - qy) ** 2 < (r + qr) ** 2:
+                ok = False
+                break
+        if ok:
+            disks.append((cx, cy, r))
+    y, x = np.mgrid[0:n, 0:n] + 0.5
+    solid = np.zeros((n, n), bool)
+    for (cx, cy, r) in disks:
+        dx = _wrap_delta(x, cx, n)
+        solid |= dx * dx + (y - cy) ** 2 < r * r
+    return (~solid).astype(np.uint8)[None]
+
+
+def sphere_pack_3d(n: int = 96, rmin: float = 6.0, rmax: float = 10.0, porosity: float = 0.35,
+                   seed: int = 0) -> np.ndarray:
+    """Spheres with radius U[rmin, rmax] at uniform random centres (x-periodic, overlap allowed),
+    added one at a time until the porosity first drops to `porosity` or below.  Returns (n, n, n)."""
+    rng = np.random.default_rng(seed)
+    solid = np.zeros((n, n, n), bool)
+    zc, yc, xc = (np.arange(n) + 0.5,) * 3
+    target = porosity * n ** 3
+    void = float(n ** 3)
+    while void > target:
+        r = rng.uniform(rmin, rmax)
+        cx, cy, cz = rng.uniform(0, n, size=3)
+        # bounding box in y and z (walls clip), x wraps
+        zlo, zhi = max(0, int(np.floor(cz - r))), min(n, int(np.ceil(cz + r)) + 1)
+        ylo, yhi = max(0, int(np.floor(cy - r))), min(n, int(np.ceil(cy + r)) + 1)
+        dz = zc[zlo:zhi, None, None] - cz
+        dy = yc[None, ylo:yhi, None] - cy
+        dx = _wrap_delta(xc[None, None, :], cx, n)
+        ball = dz * dz + dy * dy + dx * dx < r * r
+        sub = solid[zlo:zhi, ylo:yhi, :]
+        void -= np.count_nonzero(ball & ~sub)
+        sub |= ball
+    return (~solid).astype(np.uint8)
+
+
+def gaussian_field_3d(n: int = 256, corr_len: float = 8.0, porosity: float = 0.20, seed: int = 0) -> np.ndarray:
+    """Threshold of a Gaussian random field: white noise smoothed by FFT with a Gaussian kernel whose
+    covariance is exp(-r^2 / (2 l^2)) (kernel std l / sqrt(2)); void = field below its `porosity`
+    quantile.  Returns (n, n, n) uint8."""
+    rng = np.random.default_rng(seed)
+    noise = rng.standard_normal((n, n, n))
+    k = np.fft.fftfreq(n) * 2 * np.pi
+    kz, ky, kx = np.meshgrid(k, k, k, indexing="ij")
+    s = corr_len / np.sqrt(2.0)
+    filt = np.exp(-0.5 * s * s * (kx * kx + ky * ky + kz * kz))
+    field = np.real(np.fft.ifftn(np.fft.fftn(noise) * filt))
+    thr = np.quantile(field, porosity)
+    return (field < thr).astype(np.uint8)
+
+
+def channel(nx: int, ny: int, nz: int = 1, width: int | None = None) -> np.ndarray:
+    """Straight channel along x: void rows 0..width-1 in y (whole z), walls above (solid) and the
+    y box walls.  Returns (nz, ny, nx) uint8."""
+    w = ny if width is None else width
+    m = np.zeros((nz, ny, nx), np.uint8)
+    m[:, :w, :] = 1
+    return m
+
+
+# ----------------------------------------------------------------------------------------------
+# connectivity helpers (periodic seams)
+# ----------------------------------------------------------------------------------------------
+def _face_structure(ndim):
+    return ndimage.generate_binary_structure(ndim, 1)
+
+
+def _squeeze2d(mask):
+    """View of the image as 2D (ny, nx) when nz == 1, else 3D; returns (array, axis map)."""
+    if mask.shape[0] == 1:
+        return mask[0], {0: 1, 1: 0}          # solver axis -> numpy axis of the 2D array
+    return mask, {0: 2, 1: 1, 2: 0}
+
+
+def void_components(mask: np.ndarray, periodic=X_PERIODIC):
+    """Face-connected components of the void with wrap along periodic axes.
+    Returns (labels image int32 (0 = solid), count)."""
+    arr, amap = _squeeze2d(np.asarray(mask).astype(bool))
+    lab, n = ndimage.label(arr, structure=_face_structure(arr.ndim))
+    parent = np.arange(n + 1)
+
+    def find(a):
+        while parent[a] != a:
+            parent[a] = parent[parent[a]]
+            a = parent[a]
+        return a
+
+    for ax_solver, ax_np in amap.items():
+        if not periodic[ax_solver]:
+            continue
+        lo = np.take(lab, 0, axis=ax_np)
+        hi = np.take(lab, arr.shape[ax_np] - 1, axis=ax_np)
+        both = (lo > 0) & (hi > 0)
+        for a, b in zip(lo[both].ravel(), hi[both].ravel()):
+            ra, rb = find(a), find(b)
+            if ra != rb:
+                parent[max(ra, rb)] = min(ra, rb)
+    roots = np.array([find(a) for a in range(n + 1)])
+    uniq, comp = np.unique(roots, return_inverse=True)
+    comp = comp.astype(np.int32)  # root 0 (solid) maps to 0 because roots[0] == 0 is the smallest
+    out = comp[lab]
+    return out.reshape(mask.shape), len(uniq) - 1
+
+
+def percolating_void(mask: np.ndarray, periodic=X_PERIODIC):
+    """Drop void components that do not wrap around the periodic x axis (they carry no net flow).
+    A component percolates when its lift to the x-unrolled image is not simply x-bounded: some
+    cycle through the x seam has non-zero winding.  Returns (new mask, fraction of void dropped)."""
+    m = np.asarray(mask).astype(bool)
+    arr, amap = _squeeze2d(m)
+    lab, n = ndimage.label(arr, structure=_face_structure(arr.ndim))
+    # graph over non-periodic components; x-seam edges carry winding +1, other periodic seams 0
+    edges = []
+    for ax_solver, ax_np in amap.items():
+        if not periodic[ax_solver]:
+            continue
+        lo = np.take(lab, 0, axis=ax_np)
+        hi = np.take(lab, arr.shape[ax_np] - 1, axis=ax_np)
+        both = (lo > 0) & (hi > 0)
+        pairs = set(zip(hi[both].ravel().tolist(), lo[both].ravel().tolist()))
+        w = 1 if ax_solver == 0 else 0
+        edges += [(a, b, w) for (a, b) in pairs]
+    adj = {a: [] for a in range(1, n + 1)}
+    for a, b, w in edges:
+        adj[a].append((b, w))
+        adj[b].append((a, -w))
+    pot = {}
+    perc_root = {}
+    for s in range(1, n + 1):
+        if s in pot:
+            continue
+        pot[s] = 0
+        stack, members, wraps = [s], [s], False
+        while stack:
+            a = stack.pop()
+            for b, w in adj[a]:
+                if b not in pot:
+                    pot[b] = pot[a] + w
+                    stack.append(b)
+                    members.append(b)
+                elif pot[b] != pot[a] + w:
+                    wraps = True
+        for a in members:
+            perc_root[a] = wraps
+    keep = np.zeros(n + 1, bool)
+    for a, v in perc_root.items():
+        keep[a] = v
+    newarr = keep[lab] & arr
+    dropped = 1.0 - newarr.sum() / max(1, arr.sum())
+    return newarr.astype(np.uint8).reshape(mask.shape), float(dropped)
+
+
+# ----------------------------------------------------------------------------------------------
+# pore labelling: periodic EDT -> plateau markers -> priority-flood watershed
+# ----------------------------------------------------------------------------------------------
+def _pad_periodic(arr, amap, periodic, width, solid_value):
+    """Pad: wrap along periodic axes, constant `solid_value` (walls) along the others."""
+    pads = [(0, 0)] * arr.ndim
+    out = arr
+    for ax_solver, ax_np in amap.items():
+        pw = [(0, 0)] * arr.ndim
+        pw[ax_np] = (width, width)
+        if periodic[ax_solver]:
+            out = np.pad(out, pw, mode="wrap")
+        else:
+            out = np.pad(out, pw, mode="constant", constant_values=solid_value)
+        pads[ax_np] = (width, width)
+    return out, pads
+
+
+def _crop(arr, pads):
+    sl = tuple(slice(a, arr.shape[i] - b) for i, (a, b) in enumerate(pads))
+    return arr[sl]
+
+
+def distance_to_solid(mask: np.ndarray, periodic=X_PERIODIC) -> np.ndarray:
+    """Euclidean distance of each void cell to the nearest solid cell (box walls count as solid,
+    periodic axes wrap).  Shape of `mask`, float64."""
+    arr, amap = _squeeze2d(np.asarray(mask).astype(bool))
+    width = max(arr.shape)
+    padded, pads = _pad_periodic(arr, amap, periodic, width, False)
+    d = ndimage.distance_transform_edt(padded)
+    return _crop(d, pads).reshape(mask.shape)
+
+
+@dataclass
+class Labelling:
+    labels: np.ndarray      # int32, same shape as mask; 0 on solid, >= 1 on void
+    n_labels: int
+    window: int             # marker window half-width that was chosen
+    dist: np.ndarray        # distance map used as the flooding height
+
+
+def _markers(dist, arr, amap, periodic, w):
+    padded, pads = _pad_periodic(dist, amap, periodic, w, 0.0)
+    mx = ndimage.maximum_filter(padded, size=2 * w + 1, mode="constant", cval=0.0)
+    mx = _crop(mx, pads)
+    peak = arr & (dist >= mx) & (dist >= 1.0)
+    return peak
+
+
+def label_pores(mask: np.ndarray, target: int, periodic=X_PERIODIC, windows=range(1, 25)) -> Labelling:
+    """Watershed decomposition of the void into about `target` pores.
+
+    Heights are the distance map; markers are plateau components of cells that are maxima of the
+    distance within a (2w+1)-wide window (w chosen from `windows` to bring the marker count closest
+    to `target`).  A priority flood (highest distance first; ties by insertion order) grows the
+    markers over the face-connected void (wrapping along periodic axes).  Void components without a
+    marker get one at their deepest cell (lowest linear index among ties)."""
+    m = np.asarray(mask).astype(bool)
+    arr, amap = _squeeze2d(m)
+    dist2 = _squeeze2d(distance_to_solid(m, periodic))[0]
+    best = None
+    for w in windows:
+        peak = _markers(dist2, arr, amap, periodic, w)
+        plab, npk = ndimage.label(peak, structure=np.ones((3,) * arr.ndim, bool))
+        score = abs(npk - target)
+        if best is None or score < best[0]:
+            best = (score, w, plab, npk)
+        if npk < target:
+            break
+    _, w, plab, npk = best
+    flat_d = dist2.ravel()
+    shape = arr.shape
+    flat_void = arr.ravel()
+    lab = plab.ravel().astype(np.int64).copy()
+    # renumber markers by lowest linear index of their plateau
+    if npk > 0:
+        first = ndimage.minimum(np.arange(lab.size), labels=plab.ravel(), index=np.arange(1, npk + 1))
+        order = np.argsort(first, kind="stable")
+        remap = np.zeros(npk + 1, np.int64)
+        remap[order + 1] = np.arange(1, npk + 1)
+        lab = remap[lab]
+    # components without a marker
+    comp, ncomp = void_components(m, periodic)
+    comp = _squeeze2d(comp)[0].ravel()
+    has = np.zeros(ncomp + 1, bool)
+    has[comp[lab > 0]] = True
+    nl = npk
+    for cidx in range(1, ncomp + 1):
+        if not has[cidx]:
+            cells = np.flatnonzero(comp == cidx)
+            c = cells[np.argmax(flat_d[cells])]
+            nl += 1
+            lab[c] = nl
+    # neighbour offsets on the (possibly 2D) array with wrap where periodic
+    strides = np.array([int(np.prod(shape[a + 1:])) for a in range(len(shape))])
+    wraps = {ax_np: periodic[ax_s] for ax_s, ax_np in amap.items()}
+    heap = []
+    counter = 0
+    seeds = np.flatnonzero(lab > 0)
+    for c in seeds:
+        heapq.heappush(heap, (-flat_d[c], counter, int(c)))
+        counter += 1
+    coords_cache = np.unravel_index
+    while heap:
+        _, _, c = heapq.heappop(heap)
+        lc = lab[c]
+        idx = coords_cache(c, shape)
+        for ax in range(len(shape)):
+            for s in (-1, 1):
+                v = idx[ax] + s
+                if v < 0 or v >= shape[ax]:
+                    if not wraps[ax]:
+                        continue
+                    v %= shape[ax]
+                nb = c + (v - idx[ax]) * strides[ax]
+                if flat_void[nb] and lab[nb] == 0:
+                    lab[nb] = lc
+                    heapq.heappush(heap, (-flat_d[nb], counter, int(nb)))
+                    counter += 1
+    labels = lab.reshape(shape).astype(np.int32).reshape(mask.shape)
+    return Labelling(labels=labels, n_labels=int(nl), window=int(w), dist=dist2.reshape(mask.shape))
+
+
+# ----------------------------------------------------------------------------------------------
+# Reynolds number (Sec. 6)
+# ----------------------------------------------------------------------------------------------
+def characteristic_length(mask: np.ndarray, periodic=X_PERIODIC) -> float:
+    """l = V_s / A_w: solid voxel count over the count of void-solid voxel faces inside the image
+    (wrapping along periodic axes; the box walls are not counted)."""
+    m = np.asarray(mask).astype(bool)
+    arr, amap = _squeeze2d(m)
+    vs = float((~arr).sum())
+    aw = 0
+    for ax_solver, ax_np in amap.items():
+        a = arr
+        b = np.roll(arr, -1, axis=ax_np)
+        diff = a != b
+        if not periodic[ax_solver]:
+            diff = np.take(diff, np.arange(arr.shape[ax_np] - 1), axis=ax_np)
+        aw += int(diff.sum())
+    return vs / max(1, aw)
+
+
+def darcy_velocity(ux_faces: np.ndarray) -> float:
+    """U_D: mean of the x-face velocity array over the whole box (solid faces count zero)."""
+    return float(np.mean(ux_faces))
+
+
+def reynolds(mask, ux_faces, rho, mu, periodic=X_PERIODIC) -> float:
+    phi = float(np.mean(mask))
+    return rho * (darcy_velocity(ux_faces) / phi) * characteristic_length(mask, periodic) / mu
+
+
+def mu_for_reynolds(mask, ux_faces_at_mu1, re_target, rho=1.0, periodic=X_PERIODIC) -> float:
+    """Viscosity that gives `re_target` given the Stokes x-velocity computed at mu = 1 (the Stokes
+    velocity scales as 1/mu, so Re(mu) = Re(1)/mu^2)."""
+    re1 = reynolds(mask, ux_faces_at_mu1, rho, 1.0, periodic)
+    return float(np.sqrt(re1 / re_target))
+
+
+# ----------------------------------------------------------------------------------------------
+# named workloads
+# ----------------------------------------------------------------------------------------------
+@dataclass
+class Workload:
+    name: str
+    mask: np.ndarray
+    labels: np.ndarray
+    periodic: tuple
+    dropped: float
+    n_labels: int
+
+
+def make_workload(kind: str, seed: int = 0, **kw) -> Workload:
+    """Seeded image + percolation filter + labels.
+
+    kind: 'disks64'  2D 64x64, 12 non-overlapping disks r~U[4,8], ~15 pores
+          'spheres'  3D n^3 (n=96 default) sphere pack r~U[6,10] to porosity 0.35, ~200 pores
+          'grf'      3D n^3 (n=256 default) Gaussian field l=8 at porosity 0.20, ~3000 pores
+          'tiny2d' / 'tiny3d'  small disk/sphere packs for brute-force checks (n given by kw)"""
+    per = X_PERIODIC
+    if kind == "disks64":
+        n = kw.get("n", 64)
+        mask = disk_pack_2d(n, kw.get("n_disks", 12), 4.0, 8.0, seed)
+        target = kw.get("target", 15)
+    elif kind == "spheres":
+        n = kw.get("n", 96)
+        mask = sphere_pack_3d(n, kw.get("rmin", 6.0), kw.get("rmax", 10.0), kw.get("porosity", 0.35), seed)
+        target = kw.get("target", 200)
+    elif kind == "grf":
+        n = kw.get("n", 256)
+        mask = gaussian_field_3d(n, kw.get("corr_len", 8.0), kw.get("porosity", 0.20), seed)
+        target = kw.get("target", 3000)
+    elif kind == "tiny2d":
+        n = kw.get("n", 16)
+        mask = disk_pack_2d(n, kw.get("n_disks", 2), kw.get("rmin", 1.5), kw.get("rmax", 3.0), seed)
+        target = kw.get("target", 3)
+    elif kind == "tiny3d":
+        n = kw.get("n", 8)
+        mask = sphere_pack_3d(n, kw.get("rmin", 1.5), kw.get("rmax", 2.5), kw.get("porosity", 0.6), seed)
+        target = kw.get("target", 3)
+    else:
+        raise ValueError(kind)
+    mask, dropped = percolating_void(mask, per)
+    lab = label_pores(mask, target, per)
+    return Workload(kind, mask, lab.labels, per, dropped, lab.n_labels)
