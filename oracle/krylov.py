@@ -69,11 +69,12 @@ def fgmres(matvec, precond, b, tol_abs, restart=100, maxit=2000):
 class Problem:
     """Geometry + parameters + maps of one solve."""
 
-    def __init__(self, mask, labels, prm: mac.Params, periodic=(True, False, False), n_dilate=2, n_tag=1):
+    def __init__(self, mask, labels, prm: mac.Params, periodic=(True, False, False), n_dilate=1, n_tag=1,
+                 iface_mode="pair"):
         self.g = mac.Grid(mask, periodic)
         self.prm = prm
         self.pins = mac.pressure_pins(self.g)
-        self.maps = build_maps(self.g, labels, self.pins, n_dilate, n_tag)
+        self.maps = build_maps(self.g, labels, self.pins, n_dilate, n_tag, iface_mode)
         self.r0 = mac.reference_norm(self.g, prm, self.pins)
 
     def residual(self, x, x_prev=None):

@@ -25,8 +25,6 @@ that are not unknowns are zero.
 """
 from __future__ import annotations
 
-from collections import deque
-
 import numpy as np
 import scipy.sparse as sp
 
@@ -93,25 +91,34 @@ class Grid:
         return safe, valid & self.face_unknown[d][safe]
 
 
+def void_adjacency(g: Grid):
+    """Symmetric 0/1 matrix (ncell x ncell, CSR) linking face-neighbouring void cells (wrapping along
+    periodic axes)."""
+    rows, cols = [], []
+    c = np.arange(g.ncell)
+    for a in range(g.dim):
+        n = g.nb[a][1]
+        ok = g.void & (n >= 0)
+        ok &= g.void[np.where(n >= 0, n, 0)]
+        rows.append(c[ok])
+        cols.append(n[ok])
+    r = np.concatenate(rows)
+    k = np.concatenate(cols)
+    A = sp.coo_matrix((np.ones(2 * len(r)), (np.concatenate([r, k]), np.concatenate([k, r]))),
+                      shape=(g.ncell, g.ncell)).tocsr()
+    A.data[:] = 1.0
+    return A
+
+
 def pressure_pins(g: Grid):
     """Lowest-linear-index cell of every face-connected void component (periodic wrap)."""
-    seen = np.zeros(g.ncell, bool)
+    from scipy.sparse.csgraph import connected_components
+    n, lab = connected_components(void_adjacency(g), directed=False)
+    lab = np.where(g.void, lab, -1)
     pins = []
-    for s in range(g.ncell):
-        if not g.void[s] or seen[s]:
-            continue
-        pins.append(s)
-        seen[s] = True
-        q = deque([s])
-        while q:
-            c = q.popleft()
-            for a in range(g.dim):
-                for t in (0, 1):
-                    n = g.nb[a][t][c]
-                    if n >= 0 and g.void[n] and not seen[n]:
-                        seen[n] = True
-                        q.append(n)
-    return np.array(pins, dtype=np.int64)
+    for comp in np.unique(lab[g.void]):
+        pins.append(int(np.flatnonzero(lab == comp)[0]))
+    return np.array(sorted(pins), dtype=np.int64)
 
 
 class Params:

@@ -3,26 +3,37 @@
 Readings fixed where the paper is silent (listed in the design doc):
 
 * Contact interfaces (Sec. 3.2.2, "thinnest 4-/6-connected collection of pixels that separate two
-  primary grids"): a void cell of label a is an interface cell when a face-neighbour (wrapping along
-  periodic axes) is void with a label b > a; its pair is (a, smallest such b).  Interfaces are the
-  face-connected components of interface cells sharing a pair, numbered by their lowest cell index.
+  primary grids", one interface Gamma_ij per pair of adjacent primary grids): a void cell of label a
+  is an interface cell when a face-neighbour (wrapping along periodic axes) is void with a label
+  b > a; its pair is (a, smallest such b).  The interface of a pair is the set of all interface cells
+  with that pair (connected or not), numbered by its lowest cell index.  iface_mode="component"
+  splits each pair's set into face-connected components instead (an alternative reading kept for
+  comparison: on 3D sphere packs it gives ~4x more, much smaller interfaces and a far weaker
+  preconditioner).
 * Primary grid of label a = its cells that are not interface cells; labels that keep at least one
   cell are numbered in ascending label order (others are dropped and counted).
 * Faces (Sec. 3.2.2): a face unknown with at least one flanking cell in primary grid i belongs to i
   (two different primary grids never flank one face); a face flanked by two interface cells is an
   interface face ("f").
 * C^{p_i} = interfaces owning a cell face-adjacent to a cell of p_i (sorted ascending).
-* Dual grid j (Sec. 3.2.1): cells of interface j dilated `n_dilate` times over face-neighbouring void
-  cells; its unknowns are those cells and every face unknown with a flanking cell among them.
+* Coarse interfaces: an interface adjacent to no primary grid (possible at 3D junctions, where all its
+  neighbours are interface cells of other pairs) has no shape vector, so its column of P^ would be
+  the bare cell indicator and A^o singular; only interfaces in some C^{p_i} get a coarse unknown, in
+  ascending order.  The cells of the others get zero from M_G (like interface faces).
+* Dual grid j (Sec. 3.2.1): cells of interface j dilated `n_dilate` times (default 1: the dual grids
+  then cover 20-25% of the unknowns, inside the 10-30% the paper states in Sec. 7) over
+  face-neighbouring void cells; its unknowns are those cells and every face unknown with a flanking
+  cell among them.
 * gPLMM tags (Sec. 4, "faces within a few layers of each contact interface", 3-point stencil):
   every f face, plus every primary face whose same-component neighbour along some axis is an unknown
   outside its own primary grid; `n_tag` > 1 adds faces adjacent (same rule) to tagged faces.
 """
 from __future__ import annotations
 
-from collections import deque
-
 import numpy as np
+import scipy.sparse as sp
+
+from .mac import void_adjacency as mac_void_adjacency
 
 F_FACE = -1        # face class of interface (f) faces
 NOT_UNKNOWN = -2
@@ -32,7 +43,7 @@ class Maps:
     pass
 
 
-def build_maps(g, labels, pins, n_dilate=2, n_tag=1):
+def build_maps(g, labels, pins, n_dilate=1, n_tag=1, iface_mode="pair"):
     L = np.asarray(labels).ravel().astype(np.int64)
     if np.any(L[g.void] < 1) or np.any(L[~g.void] != 0):
         raise ValueError("labels must be >= 1 on void cells and 0 on solid cells")
@@ -51,30 +62,32 @@ def build_maps(g, labels, pins, n_dilate=2, n_tag=1):
             partner = np.minimum(partner, cand)
     is_if = g.void & (partner < big)
     # --- interfaces: components of same-pair interface cells
+    from scipy.sparse.csgraph import connected_components
+    adj = mac_void_adjacency(g).tocoo()
+    if iface_mode == "component":
+        same = is_if[adj.row] & is_if[adj.col] & (L[adj.row] == L[adj.col]) & (partner[adj.row] == partner[adj.col])
+        sub = sp.coo_matrix((np.ones(int(same.sum())), (adj.row[same], adj.col[same])), shape=(g.ncell, g.ncell))
+        _, comp = connected_components(sub.tocsr(), directed=False)
+    else:
+        # one interface per label pair (a, b): all interface cells with that pair, connected or not
+        key = np.where(is_if, L * (int(L.max()) + 2) + np.where(is_if, partner, 0), -1)
+        _, comp = np.unique(key, return_inverse=True)
     iface = np.full(g.ncell, -1, np.int64)
-    n_if = 0
-    for s in np.flatnonzero(is_if):
-        if iface[s] >= 0:
-            continue
-        key = (L[s], partner[s])
-        iface[s] = n_if
-        q = deque([s])
-        while q:
-            c = q.popleft()
-            for a in range(g.dim):
-                for t in (0, 1):
-                    n = g.nb[a][t][c]
-                    if n >= 0 and is_if[n] and iface[n] < 0 and (L[n], partner[n]) == key:
-                        iface[n] = n_if
-                        q.append(n)
-        n_if += 1
+    cells_if = np.flatnonzero(is_if)                     # ascending
+    uniq, first = np.unique(comp[cells_if], return_index=True)   # first = lowest cell of each component
+    order = np.argsort(cells_if[first], kind="stable")   # number components by their lowest cell
+    rank = np.empty(len(uniq), np.int64)
+    rank[order] = np.arange(len(uniq))
+    iface[cells_if] = rank[np.searchsorted(uniq, comp[cells_if])]
+    n_if = len(uniq)
     m.n_iface = n_if
     m.cell_iface = iface
     m.iface_pair = np.zeros((n_if, 2), np.int64)
+    srt = cells_if[np.argsort(iface[cells_if], kind="stable")]
+    m.iface_cells = np.split(srt, np.cumsum(np.bincount(iface[cells_if], minlength=n_if))[:-1]) if n_if else []
     for j in range(n_if):
-        c = np.flatnonzero(iface == j)[0]
+        c = m.iface_cells[j][0]
         m.iface_pair[j] = (L[c], partner[c])
-    m.iface_cells = [np.flatnonzero(iface == j) for j in range(n_if)]
     # --- primary grids
     prim_cells = g.void & ~is_if
     labs = np.unique(L[prim_cells])
@@ -107,38 +120,36 @@ def build_maps(g, labels, pins, n_dilate=2, n_tag=1):
                 if n >= 0 and cell_prim[n] >= 0:
                     cp[cell_prim[n]].add(int(iface[c]))
     m.C = [np.array(sorted(s), np.int64) for s in cp]
+    used = sorted(set(int(j) for C in m.C for j in C))
+    m.coarse_ifaces = np.array(used, np.int64)
+    m.coarse_of_iface = np.full(m.n_iface, -1, np.int64)
+    m.coarse_of_iface[m.coarse_ifaces] = np.arange(len(used))
     # --- unknown lists (global indices, ascending: faces by axis, then cells)
-    m.prim_unknowns = []
-    for i in range(m.n_prim):
-        parts = [g.fidx(d, np.flatnonzero(m.face_class[d] == i)) for d in range(g.dim)]
-        parts.append(g.pidx(np.flatnonzero(cell_prim == i)))
-        m.prim_unknowns.append(np.concatenate(parts))
+    own_all = np.concatenate(m.face_class + [np.where(cell_prim >= 0, cell_prim, NOT_UNKNOWN)])
+    glob = np.flatnonzero(own_all >= 0)                   # ascending global index
+    srt = glob[np.argsort(own_all[glob], kind="stable")]  # grouped by primary grid, ascending inside
+    m.prim_unknowns = np.split(srt, np.cumsum(np.bincount(own_all[glob], minlength=m.n_prim))[:-1])
     m.f_faces = np.concatenate([g.fidx(d, np.flatnonzero(m.face_class[d] == F_FACE)) for d in range(g.dim)])
     # --- dual grids
+    adj_csr = mac_void_adjacency(g)
     m.dual_unknowns = []
     m.dual_cells = []
     for j in range(n_if):
-        inset = np.zeros(g.ncell, bool)
-        inset[m.iface_cells[j]] = True
+        cells = m.iface_cells[j]
         for _ in range(n_dilate):
-            grow = inset.copy()
-            for a in range(g.dim):
-                for t in (0, 1):
-                    n = g.nb[a][t]
-                    ok = inset & (n >= 0)
-                    tgt = n[ok]
-                    tgt = tgt[g.void[tgt]]
-                    grow[tgt] = True
-            inset = grow
+            nbrs = adj_csr[cells].indices
+            cells = np.union1d(cells, nbrs)
+        inset = np.zeros(g.ncell, bool)
+        inset[cells] = True
         parts = []
         for d in range(g.dim):
-            lo = g.nb[d][0]
-            los = np.where(lo >= 0, lo, 0)
-            sel = g.face_unknown[d] & (inset | ((lo >= 0) & inset[los]))
-            parts.append(g.fidx(d, np.flatnonzero(sel)))
-        parts.append(g.pidx(np.flatnonzero(inset)))
+            # faces stored at c (low face of c) and at c + e_d (high face of c) for every c in the set
+            hi = g.nb[d][1][cells]
+            cand = np.union1d(cells, hi[hi >= 0])
+            parts.append(g.fidx(d, cand[g.face_unknown[d][cand]]))
+        parts.append(g.pidx(cells))
         m.dual_unknowns.append(np.concatenate(parts))
-        m.dual_cells.append(np.flatnonzero(inset))
+        m.dual_cells.append(cells)
     # --- gPLMM tags
     tags = [np.zeros(g.ncell, bool) for _ in range(g.dim)]
     for d in range(g.dim):

@@ -21,9 +21,10 @@ Two independent formulations are given:
   Eqs. 6 and 9, Q of Eq. 11, P of Eq. 14, R of Eq. 18 and E/R of Eq. 25 as explicit matrices,
   multiplied out densely.
 
-Readings: f faces get zero in P^ (no Eq. 8 back-substitution); Pi(C^T) is the structural
+Readings: f faces get zero in P^ (no Eq. 8 back-substitution); interfaces adjacent to no
+primary grid get no coarse unknown (their cells get zero in P^ and no row of R^); Pi(C^T) is the structural
 pattern of C (every unknown of p_i); b_B = -r(u=0, p=0) with the previous time level zero, i.e. rho b
-on face rows and 0 on cell rows; the coarse unknowns are ordered [x^o (interfaces); y^o (primary)].
+on face rows and 0 on cell rows; the coarse unknowns are ordered [x^o (coarse interfaces); y^o (primary)].
 """
 from __future__ import annotations
 
@@ -63,7 +64,8 @@ class Plmm:
     def __init__(self, g, prm, m, A_b, use_coarse=True):
         self.g, self.m = g, m
         self.use_coarse = use_coarse
-        self.n_o = m.n_iface + m.n_prim
+        self.n_ci = len(m.coarse_ifaces)
+        self.n_o = self.n_ci + m.n_prim
         self.lu_p = [spla.splu(A_b[P][:, P].tocsc()) for P in m.prim_unknowns]
         self.lu_d = [spla.splu(A_b[D][:, D].tocsc()) for D in m.dual_unknowns]
         if not use_coarse:
@@ -84,30 +86,30 @@ class Plmm:
                 s = -lu_bar.solve(rhs)
                 sh[int(j)] = s
                 prow.append(Pi)
-                pcol.append(np.full(len(Pi), j))
+                pcol.append(np.full(len(Pi), m.coarse_of_iface[j]))
                 pval.append(s)
             c = lu_bar.solve(bB[Pi])
             self.shape.append(sh)
             self.corr.append(c)
             prow.append(Pi)
-            pcol.append(np.full(len(Pi), m.n_iface + i))
+            pcol.append(np.full(len(Pi), self.n_ci + i))
             pval.append(c)
-        for j in range(m.n_iface):
+        for k, j in enumerate(m.coarse_ifaces):
             cells = g.pidx(m.iface_cells[j])
             prow.append(cells)
-            pcol.append(np.full(len(cells), j))
+            pcol.append(np.full(len(cells), k))
             pval.append(np.ones(len(cells)))
         self.Phat = sp.csr_matrix((np.concatenate(pval), (np.concatenate(prow), np.concatenate(pcol))),
                                   shape=(g.nfull, self.n_o))
         # restriction R^ (n_o x nfull): interface rows sum their cells, primary rows all unknowns of p_i
         rrow, rcol = [], []
-        for j in range(m.n_iface):
+        for k, j in enumerate(m.coarse_ifaces):
             cells = g.pidx(m.iface_cells[j])
-            rrow.append(np.full(len(cells), j))
+            rrow.append(np.full(len(cells), k))
             rcol.append(cells)
         for i in range(m.n_prim):
             Pi = m.prim_unknowns[i]
-            rrow.append(np.full(len(Pi), m.n_iface + i))
+            rrow.append(np.full(len(Pi), self.n_ci + i))
             rcol.append(Pi)
         rr = np.concatenate(rrow)
         self.Rhat = sp.csr_matrix((np.ones(len(rr)), (rr, np.concatenate(rcol))), shape=(self.n_o, g.nfull))
@@ -160,8 +162,9 @@ def literal_preconditioner(g, prm, m, A_b, A_solve, use_coarse=True):
     As = A_solve[unk][:, unk].toarray()
     # permuted order [p_1 .. p_n | c_1 .. c_m | f]
     p_lists = [pos[P] for P in m.prim_unknowns]
-    c_lists = [pos[g.pidx(m.iface_cells[j])] for j in range(m.n_iface)]
-    f_list = pos[m.f_faces]
+    c_lists = [pos[g.pidx(m.iface_cells[j])] for j in m.coarse_ifaces]
+    orphan = [pos[g.pidx(m.iface_cells[j])] for j in range(m.n_iface) if m.coarse_of_iface[j] < 0]
+    f_list = np.concatenate([pos[m.f_faces]] + orphan).astype(np.int64)
     order = np.concatenate(p_lists + c_lists + [f_list]).astype(np.int64)
     assert len(order) == N and len(np.unique(order)) == N
     W = np.zeros((N, N))
@@ -187,11 +190,12 @@ def literal_preconditioner(g, prm, m, A_b, A_solve, use_coarse=True):
         Abar_pp[si, si] = At_pp[si, si] + np.diag(off)
     Abar = np.block([[Abar_pp, Apc], [Acp, At_cc]])       # Eq. 10
     # Eq. 11: Q
-    Qo = np.zeros((Nc, m.n_iface))
+    nci = len(c_lists)
+    Qo = np.zeros((Nc, nci))
     cb = np.cumsum([0] + [len(l) for l in c_lists])
-    for j in range(m.n_iface):
+    for j in range(nci):
         Qo[cb[j]:cb[j + 1], j] = 1.0
-    Q = np.block([[np.eye(Np), np.zeros((Np, m.n_iface))], [np.zeros((Nc, Np)), Qo]])
+    Q = np.block([[np.eye(Np), np.zeros((Np, nci))], [np.zeros((Nc, Np)), Qo]])
     AM = Q.T @ Abar @ Q                                   # Eq. 12
     Abar_pc = AM[:Np, Np:]
     Abar_pp_M = AM[:Np, :Np]
@@ -204,12 +208,12 @@ def literal_preconditioner(g, prm, m, A_b, A_solve, use_coarse=True):
     for i in range(m.n_prim):
         si = slice(bounds[i], bounds[i + 1])
         Cm[si, i] = np.linalg.solve(Abar_pp_M[si, si], bB_p[si])
-    Pm = np.block([[B, Cm], [np.eye(m.n_iface), np.zeros((m.n_iface, m.n_prim))]])   # Eq. 14
+    Pm = np.block([[B, Cm], [np.eye(nci), np.zeros((nci, m.n_prim))]])   # Eq. 14
     # Eq. 18 with the structural pattern of C
     PiCT = np.zeros((m.n_prim, Np))
     for i in range(m.n_prim):
         PiCT[i, bounds[i]:bounds[i + 1]] = 1.0
-    Rm = np.block([[np.zeros((m.n_iface, Np)), np.eye(m.n_iface)], [PiCT, np.zeros((m.n_prim, m.n_iface))]])
+    Rm = np.block([[np.zeros((nci, Np)), np.eye(nci)], [PiCT, np.zeros((m.n_prim, nci))]])
     # Eq. 21: P^ = W Q P (f rows zero), R^ = R Q^T W^T (f columns dropped)
     QP = Q @ Pm
     QP_full = np.vstack([QP, np.zeros((N - Np - Nc, QP.shape[1]))])

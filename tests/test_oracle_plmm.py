@@ -193,3 +193,31 @@ def test_newton_fgmres_on_c1(c1_workload):
     for _ in range(10):
         xd += pb.direct_step(xd)
     assert np.linalg.norm(x - xd) / np.linalg.norm(xd) < 1e-9
+
+
+def test_orphan_interface_gets_no_coarse_unknown():
+    """3 x 5, x-periodic.  Cell (1,2) (label 1) touches only interface cells of pair (2,3) and solid,
+    so its interface (pair (1,2)) is adjacent to no primary grid.  It must get no coarse unknown: the
+    coarse matrix stays nonsingular and the literal and recipe forms still agree."""
+    lab = np.array([[3, 3, 0, 3, 3],
+                    [2, 2, 1, 2, 2],
+                    [3, 3, 0, 3, 3]])
+    mask = (lab > 0).astype(np.uint8)[None]
+    pb = krylov.Problem(mask, lab[None].astype(np.int32), mac.Params(1.0, 0.5, (1.0, 0.0)))
+    m = pb.maps
+    # hand-derived: interface 0 = pair (2,3) cells {5, 6, 8, 9}; interface 1 = pair (1,2) cell {7}
+    assert [sorted(c.tolist()) for c in m.iface_cells] == [[5, 6, 8, 9], [7]]
+    assert list(m.dropped_labels) == [1, 2]        # every cell of labels 1 and 2 is an interface cell
+    assert [list(c) for c in m.C] == [[0]]
+    assert list(m.coarse_ifaces) == [0] and list(m.coarse_of_iface) == [0, -1]
+    x = krylov.stokes_solution(pb)
+    for variant in ["gplmm", "aplmm_s"]:
+        M, A_b = pb.preconditioner(variant, x)
+        assert M.n_o == 2
+        assert np.isfinite(np.linalg.cond(M.Ao)) and np.linalg.cond(M.Ao) < 1e12
+        Mlit, _, unk = plmm.literal_preconditioner(pb.g, pb.prm, m, A_b, A_b)
+        v = np.zeros(pb.g.nfull)
+        v[unk] = np.random.default_rng(0).standard_normal(len(unk))
+        zl = Mlit @ v[unk]
+        assert np.linalg.norm(M.apply(v, A_b)[unk] - zl) / np.linalg.norm(zl) < 1e-11
+        assert M.coarse(v)[pb.g.pidx(7)] == 0.0
