@@ -1,0 +1,187 @@
+/*
+ * pns.h -- C ABI of libpns: Newton-FGMRES for MAC-discretised incompressible Navier-Stokes on a
+ * voxel image, preconditioned by the pore-level multiscale preconditioners gPLMM, aPLMM_NS and
+ * aPLMM_S of Li & Mehmani, "Preconditioning and Reduced-Order Modeling of Navier-Stokes Equations
+ * in Complex Porous Microstructures" (arXiv 2510.22077).  Single GPU (NVIDIA GB300, sm_103a).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Image: shape (nz, ny, nx), C order, x fastest; nz == 1 selects 2D.  Solver axis 0 = x, 1 = y,
+ * 2 = z.  Grid spacing h = 1.
+ *
+ * Vectors ("full layout"): device pointers to double arrays of length (dim + 1) * ncell with
+ * ncell = nx*ny*nz, blocks [u_x | u_y | (u_z) | p], each image-shaped.  The face array of axis d
+ * at cell c holds the velocity on the LOW face of c along d (between c - e_d and c).  A face is an
+ * unknown iff both flanking cells exist and are void (wrapping along periodic axes); a cell is an
+ * unknown iff it is void.  Entries that are not unknowns are ignored on input and written as 0 on
+ * output.  The caller owns every vector; the library never frees or retains caller pointers.
+ *
+ * Discretisation (Sec. 2 and Eq. 1 of the paper; readings where the paper is silent):
+ *   momentum row of face q (axis d):  rho/dt (q - q_prev) [transient]
+ *       + rho * sum_a upwind(U_a; q)          (advective (u.grad)u, first-order 3-point upwind)
+ *       + mu  * sum_a (2q - q_{+a} - q_{-a})  (missing neighbour: 0 along d, ghost -q across d)
+ *       + (p_c - p_{c-e_d}) - rho * b_d
+ *   continuity row of cell c: sum_a (u_a(high face) - u_a(low face)); in each face-connected
+ *   void component the cell with the lowest linear index is pinned instead: row = p.
+ *
+ * Execution: every call enqueues work on the stream given in pns_options.stream (NULL = the
+ * legacy default stream) and, unless stated, returns without synchronising.
+ *
+ * Errors: every int-returning call returns PNS_OK (0) or a negative PNS_ERR_* code; the message
+ * is kept in the context (pns_last_error).  No call aborts the process.  After PNS_ERR_CUDA the
+ * context should be destroyed.
+ */
+#ifndef PNS_H
+#define PNS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Opaque solver context; owned by the library (pns_setup creates it, pns_destroy frees it). */
+typedef struct pns_ctx pns_ctx;
+
+enum pns_status {
+  PNS_OK = 0,
+  PNS_ERR_ARG = -1,           /* bad argument (NULL pointer, bad size, labels inconsistent with mask) */
+  PNS_ERR_CUDA = -2,          /* a CUDA runtime call failed */
+  PNS_ERR_OOM = -3,           /* device or host allocation failed */
+  PNS_ERR_SINGULAR = -4,      /* zero or non-finite pivot in a local or coarse factor */
+  PNS_ERR_NOT_CONVERGED = -5, /* Newton or FGMRES hit its iteration cap; outputs are still written */
+  PNS_ERR_NAN = -6,           /* NaN/Inf in a residual norm */
+  PNS_ERR_STATE = -7,         /* call made in the wrong state (e.g. apply before build) */
+  PNS_ERR_TIMEOUT = -8        /* a device wait hit its limit */
+};
+
+/* Preconditioner family (Sec. 3-4):
+ *   GPLMM    build matrix = Jacobian of the modified residual (Eq. 27): inertia w . grad u with the
+ *            wind w = velocity of the linearisation state, inertia removed on tagged faces;
+ *   APLMM_NS build matrix = Newton Jacobian at the linearisation state;
+ *   APLMM_S  build matrix = Stokes Jacobian (inertia dropped, rho/dt kept);
+ *   ML_ONLY  the dual-primary smoother alone (Eq. 24) built from the gPLMM matrix (no M_G). */
+enum pns_variant { PNS_GPLMM = 0, PNS_APLMM_NS = 1, PNS_APLMM_S = 2, PNS_ML_ONLY = 3 };
+
+/* Storage / arithmetic precision of the preconditioner (local inverses, basis, coarse inverse,
+ * inner residual updates).  The Newton residual, the outer Jacobian, Arnoldi and Givens are FP64. */
+enum pns_precision { PNS_FP64 = 0, PNS_FP32 = 1, PNS_BF16 = 2 };
+
+/* Which operator the residual updates inside M use (Eqs. 4a and 24):
+ *   BUILD_MATRIX  the build matrix A_b (default: M is one fixed operator made from A_b);
+ *   CURRENT_J     the Newton Jacobian FGMRES is solving. */
+enum pns_combine { PNS_COMBINE_BUILD = 0, PNS_COMBINE_CURRENT = 1 };
+
+typedef struct pns_options {
+  int periodic[3];       /* wrap along x, y, z (default 1, 0, 0) */
+  int variant;           /* enum pns_variant (default PNS_GPLMM) */
+  int precision;         /* enum pns_precision (default PNS_FP64) */
+  int combine;           /* enum pns_combine (default PNS_COMBINE_BUILD) */
+  int n_dilate;          /* dual-grid dilations of each interface (default 1) */
+  int n_tag;             /* gPLMM tag layers (default 1) */
+  int restart;           /* FGMRES restart length m (default 100) */
+  int max_fgmres;        /* FGMRES iterations per Newton step (default 2000) */
+  int max_newton;        /* Newton iterations (default 30) */
+  double inner_tol;      /* FGMRES: stop when ||J d + r|| < inner_tol * ||r(0)|| (default 1e-9) */
+  double newton_tol;     /* Newton: stop when ||r(x)|| < newton_tol * ||r(0)|| (default 1e-8) */
+  int refine_steps;      /* Newton-Schulz steps X <- X + X (I - A X) (FP64 residual) applied to the
+                            FP32 local inverses, each block refined while its residual keeps falling fast;
+                            -1 = automatic (up to 3 for FP32/BF16; FP64 inverts in FP64) */
+  int timing;            /* 1: record CUDA events around the local-solve kernels (pns_stats) */
+  void* stream;          /* cudaStream_t to enqueue on (NULL = legacy default stream) */
+} pns_options;
+
+typedef struct pns_stats {
+  int newton_its;                 /* Newton iterations taken */
+  int fgmres_its_total;           /* FGMRES iterations summed over Newton steps */
+  int fgmres_its[64];             /* per Newton step (first 64) */
+  double res_hist[65];            /* ||r(x_k)|| / ||r(0)|| for k = 0 .. newton_its */
+  double r0_norm;                 /* ||r(u=0, p=0)|| */
+  double t_setup_ms;              /* maps + uploads (pns_setup) */
+  double t_mg_ms;                 /* M_G build: closure/shape/correction vectors, coarse matrix */
+  double t_ml_ms;                 /* M_L build: local block assembly, inversion, refinement */
+  double t_sol_ms;                /* FGMRES self time (all Newton steps) */
+  double t_local_ms;              /* time inside the batched local-solve kernels (timing == 1) */
+  long long local_launches;       /* number of batched local-solve launches timed */
+  double local_bytes_per_apply;   /* algorithmic bytes of one M_d + M_p local-solve pass */
+} pns_stats;
+
+typedef struct pns_info {
+  int nx, ny, nz, dim;
+  long long ncell, n_unknowns, n_faces, n_cells;
+  int n_prim, n_iface, n_pins, n_dropped_labels;
+  long long prim_unknowns_total, dual_unknowns_total;
+  double prim_sum_n2, dual_sum_n2;  /* sum of squared block sizes (dense inverse entries) */
+  int max_block;
+  size_t device_bytes;              /* bytes the context holds on the device */
+} pns_info;
+
+/* Fill `opt` with the defaults listed above. */
+void pns_default_options(pns_options* opt);
+
+/* Create a context.  mask: HOST uint8 array (nz*ny*nx), 1 = void.  subdomain_labels: HOST int32
+ * array, >= 1 on void cells, 0 on solid cells (PNS_ERR_ARG otherwise); labels need not be
+ * consecutive (primary grids are numbered in ascending label order).  rho, mu > 0; b[3] body force
+ * per unit mass; dt <= 0 selects the steady equations, dt > 0 backward Euler with step dt.
+ * Builds the integer maps of Sec. 3.2.1-3.2.2 and Sec. 4 (pins, contact interfaces, face classes,
+ * dual grids, gPLMM tags) and uploads them.  Copies its inputs.  Synchronises. */
+int pns_setup(pns_ctx** out, int nz, int ny, int nx, const uint8_t* mask,
+              const int32_t* subdomain_labels, double rho, double mu, const double b[3], double dt,
+              const pns_options* opt);
+
+/* Free everything the context holds.  NULL is accepted. */
+void pns_destroy(pns_ctx* ctx);
+
+/* Message of the last error on this context ("" if none).  Valid until the next call. */
+const char* pns_last_error(const pns_ctx* ctx);
+
+int pns_get_info(const pns_ctx* ctx, pns_info* info);
+
+/* r = r(x) (Eq. 3): the Newton residual in FP64.  x_prev: previous time level (device, full
+ * layout) for backward Euler, or NULL (steady, or transient with u_prev = 0). */
+int pns_residual(pns_ctx* ctx, const double* x, const double* x_prev, double* r);
+
+/* y = J(x_lin) v: the Newton Jacobian at x_lin, upwind branches frozen at x_lin (FP64). */
+int pns_jacobian_apply(pns_ctx* ctx, const double* x_lin, const double* v, double* y);
+
+/* y = A v for the build-matrix operator of a variant (enum pns_variant; ML_ONLY = GPLMM) at the
+ * linearisation state x_lin (FP64).  Exposed for testing the gPLMM modified Jacobian (Eq. 27). */
+int pns_operator_apply(pns_ctx* ctx, int variant, const double* x_lin, const double* v, double* y);
+
+/* Build the preconditioner of opt.variant at the linearisation state x_lin (device, full layout):
+ * local blocks of the primary and dual grids (Eq. 25) assembled densely and inverted, closure
+ * blocks (Eqs. 6 and 9), shape and correction vectors (Eqs. 15 and 17), coarse matrix
+ * A^o = R^ A_b P^ (Remark 1) and its inverse.  Synchronises. */
+int pns_build_precond(pns_ctx* ctx, const double* x_lin);
+
+/* z = M^{-1} v (Eqs. 4a, 24, 25, 20): FP64 in and out, internal precision opt.precision.
+ * PNS_ERR_STATE before pns_build_precond. */
+int pns_precond_apply(pns_ctx* ctx, const double* v, double* z);
+
+/* Newton-FGMRES (Sec. 8).  x: device, full layout; initial guess on input, solution on output.
+ * x_prev: previous time level (transient) or NULL.  Builds the preconditioner at the initial
+ * guess if none is built.  st may be NULL.  Synchronises.  PNS_ERR_NOT_CONVERGED if max_newton is
+ * reached (x holds the last iterate). */
+int pns_newton_solve(pns_ctx* ctx, double* x, const double* x_prev, pns_stats* st);
+
+/* Stokes solution (inertia dropped, rho b kept): the initial Newton iterate of Sec. 4 when no
+ * nearby wind exists.  Builds an aPLMM_S preconditioner internally (kept separately from the one
+ * of pns_build_precond) and runs FGMRES on the linear system.  x: device, output.  Synchronises. */
+int pns_stokes_solve(pns_ctx* ctx, double* x, pns_stats* st);
+
+/* Copy the integer maps to HOST arrays (for bit-exact tests).  Any pointer may be NULL.
+ *   cell_prim[ncell]   primary grid of each cell (-1: interface cell or solid)
+ *   cell_iface[ncell]  contact interface of each cell (-1: none)
+ *   face_class[dim*ncell]  per axis: primary grid of the face, -1 interface face (f), -2 not an unknown
+ *   tags[dim*ncell]    1 where the gPLMM modified residual drops the inertia
+ *   dual_count[(dim+1)*ncell]  number of dual grids containing each unknown
+ *   pins[n_pins]       pinned cells (ascending) */
+int pns_export_maps(const pns_ctx* ctx, int32_t* cell_prim, int32_t* cell_iface, int32_t* face_class,
+                    uint8_t* tags, int32_t* dual_count, int32_t* pins);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PNS_H */

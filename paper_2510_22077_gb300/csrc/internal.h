@@ -1,0 +1,163 @@
+// Internal types of libpns: device buffers, the preconditioner, the context and the kernel launchers.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/pns.h"
+#include "maps.h"
+#include "stencil.cuh"
+
+namespace pns {
+
+// ---------------------------------------------------------------- device allocation helpers
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  ~DevBuf() { release(); }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+  }
+  template <typename T> T* as() const { return (T*)p; }
+};
+
+// Error carrier: kernels and launchers return cudaError_t; API functions map to pns_status.
+struct Status {
+  int code = PNS_OK;
+  std::string msg;
+};
+
+// A batch of dense local blocks (primary grids, dual grids, or closure blocks).
+struct BlockSet {
+  int nblk = 0;
+  std::vector<int> n;            // block sizes
+  std::vector<int> ld;           // leading dimension of each stored matrix (row-major, padded)
+  std::vector<long long> ioff;   // offset of each block's unknown list / packed local vector
+  std::vector<long long> moff;   // offset (elements) of each block's matrix
+  long long n_total = 0;         // sum of n
+  long long m_total = 0;         // sum of n * ld
+  double sum_n2 = 0;             // sum of n^2
+  int nmax = 0;
+  DevBuf idx;                    // int32 full indices, concatenated
+  DevBuf d_n, d_ld, d_ioff, d_moff;
+  DevBuf mat;                    // inverse storage (type depends on precision)
+  // GEMV work list: (block, first row, row count)
+  int nitems = 0;
+  DevBuf items;                  // int4
+};
+
+// Preconditioner built from one build matrix A_b (pns_build_precond / the internal Stokes solve).
+struct Precond {
+  bool built = false;
+  int variant = PNS_GPLMM;
+  int precision = PNS_FP64;
+  int op = OP_OSEEN;             // stencil operator of A_b
+  DevBuf state;                  // linearisation state of A_b (FP64, full layout)
+  BlockSet prim, dual;
+  bool coarse = true;
+  int n_o = 0;                   // coarse interfaces + N^p
+  int n_cif = 0;                 // coarse interfaces (adjacent to a primary grid)
+  // basis: per primary grid a dense n_i x k_i matrix (k_i = |C_i| + 1), row-major, storage type
+  std::vector<int> kcols;
+  std::vector<long long> boff;
+  DevBuf basis, d_boff, d_kcols, d_colid, d_coloff;   // colid: coarse column of each basis column
+  DevBuf ao_inv;                 // N_o x N_o inverse of the coarse matrix (storage type)
+  // restriction segments: interface cells (by interface) then primary unknowns (by primary grid)
+  DevBuf seg_idx, seg_off;       // int32 indices, int64 offsets (n_o + 1)
+  int nseg_items = 0;
+  DevBuf seg_items;              // int2 (segment, chunk start) work list
+  double local_bytes = 0;        // algorithmic bytes of one M_d + M_p pass
+  double ns_residual_before = 0; // max |I - A X| of the local inverses before refinement
+};
+
+struct Ctx {
+  Geo G;
+  Phy P;
+  pns_options opt;
+  cudaStream_t stream = nullptr;
+  Maps M;
+  std::string err;
+  DevBuf flags;                  // uint8 per cell
+  DevBuf owner;                  // int32 per full index
+  DevBuf cell_iface;             // int32 per cell
+  long long nfull = 0;
+  Precond pc;
+  // scratch vectors (precision-dependent types; FP64 buffers sized nfull)
+  DevBuf w0, w1, w2, w3, w4;     // preconditioner internals (VT)
+  DevBuf pk_x, pk_y;             // packed local vectors (VT), sized max(prim, dual) n_total
+  DevBuf coarse_rhs, coarse_x;   // double, n_o
+  DevBuf red;                    // reduction scratch (double)
+  // Krylov workspace
+  int m_alloc = 0;
+  DevBuf V, Z, H, givens, hvec, partial;
+  DevBuf xk, rk, dx;
+  // timing
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  double t_local_ms = 0;
+  long long local_launches = 0;
+  const double* cur_state = nullptr;   // Newton state for COMBINE_CURRENT
+  double t_setup_ms = 0;
+  double t_mg_ms = 0, t_ml_ms = 0;
+};
+
+// ---------------------------------------------------------------- launchers (kernels_*.cu)
+// stencil
+cudaError_t launch_residual(const Ctx& C, int stokes, const double* x, const double* xprev, double* r);
+template <typename VT>
+cudaError_t launch_apply(const Ctx& C, int op, const double* state, const VT* v, const VT* b, VT* y, bool fp64_math);
+cudaError_t launch_cast_d2f(const double* in, float* out, long long n, cudaStream_t s);
+cudaError_t launch_cast_f2d(const float* in, double* out, long long n, cudaStream_t s);
+
+// dense local blocks
+template <typename ST>
+cudaError_t launch_assemble(const Ctx& C, const BlockSet& B, int op, const double* state, ST* mat, int closure);
+template <typename ST>
+cudaError_t launch_gj_invert(const BlockSet& B, ST* mat, int* d_bad, cudaStream_t s);
+cudaError_t launch_closure_rhs(const Ctx& C, const BlockSet& B, int op, const double* state, const int* d_colbase,
+                               const int* d_cols, const long long* d_roff, const int* d_kc, double* rhs);
+template <typename ST, typename AT>
+cudaError_t launch_block_mm(const BlockSet& B, const ST* mat, const double* rhs, const long long* d_roff,
+                            const int* d_kc, double* out, cudaStream_t s);
+template <typename ST, typename PT>
+cudaError_t launch_local_solve(const BlockSet& B, const ST* mat, const double* t, double* z, PT* pk_x, int add,
+                               cudaStream_t s);
+
+template <typename ST, typename AT>
+cudaError_t launch_ns_refine(const Ctx& C, const BlockSet& B, int op, const double* state, int closure, ST* mat,
+                             int steps, double thresh, size_t budget_bytes, double* max_before, double* max_after);
+cudaError_t launch_closure_residual(const Ctx& C, const BlockSet& B, int op, const double* state,
+                                    const long long* d_roff, const int* d_kc, const double* rhs, const double* S,
+                                    double* res);
+cudaError_t launch_add_vec(double* a, const double* b, long long n, cudaStream_t s);
+
+// coarse
+cudaError_t launch_seg_sum(const Precond& pc, const void* v, int vt_is_double, double* out, cudaStream_t s);
+template <typename ST, typename VT>
+cudaError_t launch_prolong(const Ctx& C, const Precond& pc, const double* xo, VT* z);
+cudaError_t launch_coarse_invert(double* A, int n, double* work, int* perm, int* d_bad, cudaStream_t s);
+template <typename ST>
+cudaError_t launch_coarse_gemv(const ST* Ainv, int n, const double* rhs, double* x, cudaStream_t s);
+
+// krylov (FP64)
+cudaError_t launch_multidot(const double* V, long long ld, int nvec, const double* w, long long n, double* partial,
+                            int nblocks, double* out, cudaStream_t s);
+cudaError_t launch_multi_axpy(double* w, const double* V, long long ld, int nvec, const double* h, double sign,
+                              long long n, cudaStream_t s);
+cudaError_t launch_dot(const double* a, const double* b, long long n, double* partial, double* out, cudaStream_t s);
+cudaError_t launch_scale(double* x, long long n, const double* num, const double* den, int invert, cudaStream_t s);
+cudaError_t launch_axpy(double* y, const double* x, double a, long long n, cudaStream_t s);
+cudaError_t launch_givens(double* H, int ldh, double* cs, double* sn, double* g, int j, double* resid_out,
+                          cudaStream_t s);
+cudaError_t launch_hcol(double* H, int ldh, int j, const double* h1, const double* h2, const double* hnorm,
+                        cudaStream_t s);
+cudaError_t launch_trisolve_update(const double* H, int ldh, const double* g, int k, double* y, const double* Z,
+                                   long long ld, double* x, long long n, cudaStream_t s);
+
+}  // namespace pns

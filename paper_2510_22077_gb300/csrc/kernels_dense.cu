@@ -1,0 +1,870 @@
+// Dense local blocks of the PLMM preconditioner (Eq. 25 smoother blocks, Eqs. 6/9 closure blocks):
+//  * assembly of A_b restricted to each block from the matrix-free stencil rows,
+//  * batched, variable-size, blocked Gauss-Jordan inversion without pivoting (unknowns ordered
+//    faces first, cells last, so the elimination is the velocity block followed by the pressure
+//    Schur complement; a non-finite or zero pivot raises a flag),
+//  * skinny products X * RHS (shape and correction vectors, Eqs. 15 and 17),
+//  * the batched local solve z[idx] (+)= X * t[idx] used by every preconditioner application.
+// Blocks are stored row-major with a leading dimension padded to 8 elements; padding is zero.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "internal.h"
+
+namespace pns {
+
+namespace {
+
+constexpr int TB = 64;   // Gauss-Jordan panel width == tile edge
+
+template <typename T> __device__ __forceinline__ T to_acc(T v) { return v; }
+__device__ __forceinline__ float to_f(float v) { return v; }
+__device__ __forceinline__ float to_f(__nv_bfloat16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ double to_f(double v) { return v; }
+
+__device__ __forceinline__ int find_block(const long long* __restrict__ off, int nb, long long t) {
+  int lo = 0, hi = nb - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (off[mid] <= t) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ int lower_idx(const int* __restrict__ a, int n, int key) {
+  int lo = 0, hi = n;
+  while (lo < hi) {
+    int mid = (lo + hi) >> 1;
+    if (a[mid] < key) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// small per-thread list of (column, value) with duplicates merged
+struct RowList {
+  int col[32];
+  double val[32];
+  int n;
+  __device__ void operator()(int c, double v) {
+    for (int k = 0; k < n; ++k)
+      if (col[k] == c) { val[k] += v; return; }
+    if (n < 32) { col[n] = c; val[n] = v; ++n; }
+  }
+};
+
+// ------------------------------------------------------------------------------ assembly
+template <typename ST>
+__global__ void k_assemble(Geo G, Phy P, const uint8_t* __restrict__ fl, int op, const double* __restrict__ st,
+                           const int* __restrict__ owner, int nblk, const long long* __restrict__ ioff,
+                           const int* __restrict__ bn, const int* __restrict__ bld, const long long* __restrict__ moff,
+                           const int* __restrict__ idx, long long n_total, ST* __restrict__ mat, int closure) {
+  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= n_total) return;
+  int b = find_block(ioff, nblk, t);
+  int r = (int)(t - ioff[b]);
+  int n = bn[b];
+  if (r >= n) return;                              // padding slot of the packed layout
+  const int* bidx = idx + ioff[b];
+  int g = bidx[r];
+  RowList L;
+  L.n = 0;
+  any_row<double>(G, P, fl, op, st, g, L);
+  ST* row = mat + moff[b] + (long long)r * bld[b];
+  int me = closure ? owner[g] : -100;
+  double extra = 0.0;
+  for (int k = 0; k < L.n; ++k) {
+    int lc = lower_idx(bidx, n, L.col[k]);
+    if (lc < n && bidx[lc] == L.col[k]) {
+      row[lc] = (ST)((double)row[lc] + L.val[k]);
+    } else if (closure) {
+      int o = owner[L.col[k]];
+      if (o == -3 || (o >= 0 && o != me)) extra += L.val[k];
+    }
+  }
+  if (closure) row[r] = (ST)((double)row[r] + extra);
+}
+
+// ------------------------------------------------------------------------------ Gauss-Jordan
+// step k: panel rows/cols [k*TB, k*TB + nb).  Active blocks are the first `cnt` of `order`.
+template <typename ST>
+__global__ void k_gj_diag(int k, const int* __restrict__ order, const int* __restrict__ bn,
+                          const int* __restrict__ bld, const long long* __restrict__ moff, ST* __restrict__ mat,
+                          int* __restrict__ bad) {
+  __shared__ ST D[TB][TB + 1];
+  __shared__ ST colt[TB];
+  int b = order[blockIdx.x];
+  int n = bn[b], ld = bld[b];
+  int p0 = k * TB;
+  int nb = min(TB, n - p0);
+  ST* A = mat + moff[b] + (long long)p0 * ld + p0;
+  for (int e = threadIdx.x; e < TB * TB; e += blockDim.x) {
+    int i = e / TB, j = e % TB;
+    D[i][j] = (i < nb && j < nb) ? A[(long long)i * ld + j] : (ST)0;
+  }
+  __syncthreads();
+  for (int t = 0; t < nb; ++t) {
+    ST piv = D[t][t];
+    bool okp = (piv == piv) && piv != (ST)0 && (double)fabs((double)piv) < 1e300;
+    if (!okp) {
+      if (threadIdx.x == 0) atomicExch(bad, 1);
+      piv = (ST)1;
+    }
+    ST inv = (ST)1 / piv;
+    __syncthreads();
+    for (int j = threadIdx.x; j < nb; j += blockDim.x) {
+      colt[j] = D[j][t];
+      if (j != t) D[t][j] *= inv;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) D[t][t] = inv;
+    __syncthreads();
+    for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
+      int i = e / nb, j = e % nb;
+      if (i == t) continue;
+      if (j == t) D[i][t] = -colt[i] * inv;
+      else D[i][j] -= colt[i] * D[t][j];
+    }
+    __syncthreads();
+  }
+  for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
+    int i = e / nb, j = e % nb;
+    A[(long long)i * ld + j] = D[i][j];
+  }
+}
+
+__device__ __forceinline__ int tile_skip(int t, int k) { return t + (t >= k); }
+
+// A[P, J] <- Dinv * A[P, J] for every column tile J != k
+template <typename ST>
+__global__ void k_gj_rowpanel(int k, int cnt, const int* __restrict__ order, const long long* __restrict__ pre1,
+                              const int* __restrict__ bn, const int* __restrict__ bld,
+                              const long long* __restrict__ moff, ST* __restrict__ mat) {
+  extern __shared__ unsigned char smraw[];
+  ST(*Dv)[TB + 1] = (ST(*)[TB + 1])smraw;
+  ST(*Tl)[TB + 1] = (ST(*)[TB + 1])(smraw + sizeof(ST) * TB * (TB + 1));
+  long long w = blockIdx.x;
+  int s = find_block(pre1, cnt, w);
+  int b = order[s];
+  int jt = tile_skip((int)(w - pre1[s]), k);
+  int n = bn[b], ld = bld[b];
+  int p0 = k * TB, j0 = jt * TB;
+  int nb = min(TB, n - p0), nj = min(TB, n - j0);
+  ST* A = mat + moff[b];
+  for (int e = threadIdx.x; e < TB * TB; e += blockDim.x) {
+    int i = e / TB, j = e % TB;
+    Dv[i][j] = (i < nb && j < nb) ? A[(long long)(p0 + i) * ld + p0 + j] : (ST)0;
+    Tl[i][j] = (i < nb && j < nj) ? A[(long long)(p0 + i) * ld + j0 + j] : (ST)0;
+  }
+  __syncthreads();
+  int ty = threadIdx.x / 16, tx = threadIdx.x % 16;
+  ST acc[4][4] = {};
+  for (int kk = 0; kk < nb; ++kk) {
+    ST a[4], bb[4];
+    for (int i = 0; i < 4; ++i) a[i] = Dv[ty * 4 + i][kk];
+    for (int j = 0; j < 4; ++j) bb[j] = Tl[kk][tx * 4 + j];
+    for (int i = 0; i < 4; ++i)
+      for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * bb[j];
+  }
+  __syncthreads();
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) {
+      int r = ty * 4 + i, cc = tx * 4 + j;
+      if (r < nb && cc < nj) A[(long long)(p0 + r) * ld + j0 + cc] = acc[i][j];
+    }
+}
+
+// A[I, J] -= A[I, P] * A[P, J] for tiles I != k, J != k
+template <typename ST>
+__global__ void k_gj_update(int k, int cnt, const int* __restrict__ order, const long long* __restrict__ pre2,
+                            const int* __restrict__ bn, const int* __restrict__ bld, const long long* __restrict__ moff,
+                            ST* __restrict__ mat) {
+  extern __shared__ unsigned char smraw[];
+  ST(*As)[TB + 1] = (ST(*)[TB + 1])smraw;
+  ST(*Bs)[TB + 1] = (ST(*)[TB + 1])(smraw + sizeof(ST) * TB * (TB + 1));
+  long long w = blockIdx.x;
+  int s = find_block(pre2, cnt, w);
+  int b = order[s];
+  int n = bn[b], ld = bld[b];
+  int T = (n + TB - 1) / TB;
+  long long loc = w - pre2[s];
+  int it = tile_skip((int)(loc / (T - 1)), k), jt = tile_skip((int)(loc % (T - 1)), k);
+  int p0 = k * TB, i0 = it * TB, j0 = jt * TB;
+  int nb = min(TB, n - p0), ni = min(TB, n - i0), nj = min(TB, n - j0);
+  ST* A = mat + moff[b];
+  for (int e = threadIdx.x; e < TB * TB; e += blockDim.x) {
+    int i = e / TB, j = e % TB;
+    As[i][j] = (i < ni && j < nb) ? A[(long long)(i0 + i) * ld + p0 + j] : (ST)0;
+    Bs[i][j] = (i < nb && j < nj) ? A[(long long)(p0 + i) * ld + j0 + j] : (ST)0;
+  }
+  __syncthreads();
+  int ty = threadIdx.x / 16, tx = threadIdx.x % 16;
+  ST acc[4][4] = {};
+  for (int kk = 0; kk < nb; ++kk) {
+    ST a[4], bb[4];
+    for (int i = 0; i < 4; ++i) a[i] = As[ty * 4 + i][kk];
+    for (int j = 0; j < 4; ++j) bb[j] = Bs[kk][tx * 4 + j];
+    for (int i = 0; i < 4; ++i)
+      for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * bb[j];
+  }
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) {
+      int r = ty * 4 + i, cc = tx * 4 + j;
+      if (r < ni && cc < nj) {
+        ST* q = A + (long long)(i0 + r) * ld + j0 + cc;
+        *q = *q - acc[i][j];
+      }
+    }
+}
+
+// A[I, P] <- -A[I, P] * Dinv for row tiles I != k
+template <typename ST>
+__global__ void k_gj_colpanel(int k, int cnt, const int* __restrict__ order, const long long* __restrict__ pre1,
+                              const int* __restrict__ bn, const int* __restrict__ bld,
+                              const long long* __restrict__ moff, ST* __restrict__ mat) {
+  extern __shared__ unsigned char smraw[];
+  ST(*Dv)[TB + 1] = (ST(*)[TB + 1])smraw;
+  ST(*Tl)[TB + 1] = (ST(*)[TB + 1])(smraw + sizeof(ST) * TB * (TB + 1));
+  long long w = blockIdx.x;
+  int s = find_block(pre1, cnt, w);
+  int b = order[s];
+  int it = tile_skip((int)(w - pre1[s]), k);
+  int n = bn[b], ld = bld[b];
+  int p0 = k * TB, i0 = it * TB;
+  int nb = min(TB, n - p0), ni = min(TB, n - i0);
+  ST* A = mat + moff[b];
+  for (int e = threadIdx.x; e < TB * TB; e += blockDim.x) {
+    int i = e / TB, j = e % TB;
+    Dv[i][j] = (i < nb && j < nb) ? A[(long long)(p0 + i) * ld + p0 + j] : (ST)0;
+    Tl[i][j] = (i < ni && j < nb) ? A[(long long)(i0 + i) * ld + p0 + j] : (ST)0;
+  }
+  __syncthreads();
+  int ty = threadIdx.x / 16, tx = threadIdx.x % 16;
+  ST acc[4][4] = {};
+  for (int kk = 0; kk < nb; ++kk) {
+    ST a[4], bb[4];
+    for (int i = 0; i < 4; ++i) a[i] = Tl[ty * 4 + i][kk];
+    for (int j = 0; j < 4; ++j) bb[j] = Dv[kk][tx * 4 + j];
+    for (int i = 0; i < 4; ++i)
+      for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * bb[j];
+  }
+  __syncthreads();
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) {
+      int r = ty * 4 + i, cc = tx * 4 + j;
+      if (r < ni && cc < nb) A[(long long)(i0 + r) * ld + p0 + cc] = -acc[i][j];
+    }
+}
+
+// ------------------------------------------------------------------------------ closure RHS
+// rhs (n_i x kc_i, row-major, FP64) of primary grid i: column k < kc-1 = -sum_{cells of interface
+// C_i[k]} A_b[row, cell] (so that X * rhs is the shape vector), last column = b_B (rho b_d on face
+// rows, 0 on cell rows).
+__global__ void k_closure_rhs(Geo G, Phy P, const uint8_t* __restrict__ fl, int op, const double* __restrict__ st,
+                              const int* __restrict__ cell_iface, int nblk, const long long* __restrict__ ioff,
+                              const int* __restrict__ bn, const int* __restrict__ idx, long long n_total,
+                              const int* __restrict__ colbase, const int* __restrict__ cols,
+                              const long long* __restrict__ roff, const int* __restrict__ kcv,
+                              double* __restrict__ rhs) {
+  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= n_total) return;
+  int b = find_block(ioff, nblk, t);
+  int r = (int)(t - ioff[b]);
+  if (r >= bn[b]) return;
+  int g = idx[t];
+  int kc = kcv[b];
+  double* out = rhs + roff[b] + (long long)r * kc;
+  const int* myc = cols + colbase[b];
+  RowList L;
+  L.n = 0;
+  any_row<double>(G, P, fl, op, st, g, L);
+  for (int k = 0; k < L.n; ++k) {
+    int is_cell, d, c;
+    decode(G, L.col[k], is_cell, d, c);
+    if (!is_cell) continue;
+    int j = cell_iface[c];
+    if (j < 0) continue;
+    int pos = lower_idx(myc, kc - 1, j);
+    if (pos < kc - 1 && myc[pos] == j) out[pos] -= L.val[k];
+  }
+  int is_cell, d, c;
+  decode(G, g, is_cell, d, c);
+  out[kc - 1] = is_cell ? 0.0 : P.rho * P.b[d];
+}
+
+// ------------------------------------------------------------------------------ X * RHS
+// out[b] (n x kc, FP64) = X_b (n x n) * rhs[b] (n x kc); one warp per row, 16 RHS columns at a time
+template <typename ST, typename AT>
+__global__ void k_block_mm(int nblk, const long long* __restrict__ ioff, const int* __restrict__ bn,
+                           const int* __restrict__ bld, const long long* __restrict__ moff, const ST* __restrict__ mat,
+                           long long n_total, const double* __restrict__ rhs, const long long* __restrict__ roff,
+                           const int* __restrict__ kcv, double* __restrict__ out) {
+  long long t = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (t >= n_total) return;
+  int b = find_block(ioff, nblk, t);
+  int r = (int)(t - ioff[b]);
+  int n = bn[b];
+  if (r >= n) return;
+  int kc = kcv[b];
+  const ST* X = mat + moff[b] + (long long)r * bld[b];
+  const double* R = rhs + roff[b];
+  for (int k0 = 0; k0 < kc; k0 += 16) {
+    int kn = min(16, kc - k0);
+    AT acc[16];
+    for (int q = 0; q < 16; ++q) acc[q] = (AT)0;
+    for (int cidx = lane; cidx < n; cidx += 32) {
+      AT xv = (AT)to_f(X[cidx]);
+      const double* rr = R + (long long)cidx * kc + k0;
+      for (int q = 0; q < kn; ++q) acc[q] += xv * (AT)rr[q];
+    }
+    for (int q = 0; q < kn; ++q) {
+      AT v = acc[q];
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) out[roff[b] + (long long)r * kc + k0 + q] = (double)v;
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------ local solve
+template <typename PT>
+__global__ void k_gather(const int* __restrict__ idx, long long n_total, const double* __restrict__ t,
+                         PT* __restrict__ pk) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= n_total) return;
+  int g = idx[i];
+  pk[i] = g >= 0 ? (PT)t[g] : (PT)0;
+}
+
+// vector load helpers: 16 bytes of the row and of x
+__device__ __forceinline__ float dot16(const float* a, const float* x) {
+  float4 u = *reinterpret_cast<const float4*>(a);
+  float4 v = *reinterpret_cast<const float4*>(x);
+  return u.x * v.x + u.y * v.y + u.z * v.z + u.w * v.w;
+}
+__device__ __forceinline__ double dot16(const double* a, const double* x) {
+  double2 u = *reinterpret_cast<const double2*>(a);
+  double2 v = *reinterpret_cast<const double2*>(x);
+  return u.x * v.x + u.y * v.y;
+}
+__device__ __forceinline__ float dot16(const __nv_bfloat16* a, const float* x) {
+  uint4 raw = *reinterpret_cast<const uint4*>(a);
+  const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&raw);
+  float4 v0 = *reinterpret_cast<const float4*>(x);
+  float4 v1 = *reinterpret_cast<const float4*>(x + 4);
+  float2 f0 = __bfloat1622float2(h[0]), f1 = __bfloat1622float2(h[1]);
+  float2 f2 = __bfloat1622float2(h[2]), f3 = __bfloat1622float2(h[3]);
+  return f0.x * v0.x + f0.y * v0.y + f1.x * v0.z + f1.y * v0.w + f2.x * v1.x + f2.y * v1.y + f3.x * v1.z +
+         f3.y * v1.w;
+}
+template <typename ST> struct VecW { static constexpr int n = 16 / sizeof(ST); };
+
+// One warp per row; item = (block, first row, rows).  z[idx[row]] = y (add: atomicAdd), z in FP64.
+// The dot products run in the packed type PT (FP32 for the FP32/BF16 inverses): per-lane partial
+// sums over n/32 terms, the 32 lane partials are added in FP64.
+template <typename ST, typename PT>
+__global__ void __launch_bounds__(256) k_local_gemv(const int4* __restrict__ items, const int* __restrict__ idx,
+                                                    const long long* __restrict__ ioff, const int* __restrict__ bld,
+                                                    const long long* __restrict__ moff, const ST* __restrict__ mat,
+                                                    const PT* __restrict__ pk, double* __restrict__ z, int add) {
+  int4 it = items[blockIdx.x];
+  int b = it.x;
+  int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ld = bld[b];
+  const PT* x = pk + ioff[b];
+  const ST* M = mat + moff[b];
+  constexpr int W = VecW<ST>::n;
+  for (int r = it.y + warp; r < it.y + it.z; r += 8) {
+    const ST* row = M + (long long)r * ld;
+    PT acc = (PT)0;
+    for (int c = lane * W; c < ld; c += 32 * W) acc += dot16(row + c, x + c);
+    double a = (double)acc;
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    if (lane == 0) {
+      int g = idx[ioff[b] + r];
+      if (add) atomicAdd(z + g, a);
+      else z[g] = a;
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------ refinement
+// Newton-Schulz step X <- X + X (I - A X) for blocks whose residual exceeds a threshold.  The
+// residual is formed in FP64 from the exact stencil coefficients of A (sparse rows), so the refined
+// inverse is accurate to the storage precision even when the Gauss-Jordan pass was run in FP32.
+//
+// Work lists address a subset of a BlockSet: entry e -> block lst[e], scratch offset soff[e].
+
+// R[r][:] = e_r - sum_k a_rk X[k][:]  (stored in the scratch of entry e, compute type AT); also
+// rmax[e] = max |R| of the block (as float bits, atomicMax on non-negative floats)
+template <typename ST, typename RT>
+__global__ void k_ns_residual(Geo G, Phy P, const uint8_t* __restrict__ fl, int op, const double* __restrict__ st,
+                              const int* __restrict__ owner, int closure, const int* __restrict__ lst,
+                              const long long* __restrict__ rowpre, int nent, const long long* __restrict__ ioff,
+                              const int* __restrict__ bn, const int* __restrict__ bld,
+                              const long long* __restrict__ moff, const int* __restrict__ idx,
+                              const ST* __restrict__ mat, const long long* __restrict__ soff, RT* __restrict__ R,
+                              unsigned int* __restrict__ rmax) {
+  __shared__ int scol[32];
+  __shared__ double sval[32];
+  __shared__ int sn;
+  long long w = blockIdx.x;
+  int e = find_block(rowpre, nent, w);
+  int b = lst[e];
+  int r = (int)(w - rowpre[e]);
+  int n = bn[b], ld = bld[b];
+  const int* bidx = idx + ioff[b];
+  if (threadIdx.x == 0) {
+    RowList L;
+    L.n = 0;
+    int g = bidx[r];
+    any_row<double>(G, P, fl, op, st, g, L);
+    int me = closure ? owner[g] : -100;
+    double extra = 0.0;
+    int m = 0;
+    int diagpos = -1;
+    for (int k = 0; k < L.n; ++k) {
+      int lc = lower_idx(bidx, n, L.col[k]);
+      if (lc < n && bidx[lc] == L.col[k]) {
+        scol[m] = lc;
+        sval[m] = L.val[k];
+        if (lc == r) diagpos = m;
+        ++m;
+      } else if (closure) {
+        int o = owner[L.col[k]];
+        if (o == -3 || (o >= 0 && o != me)) extra += L.val[k];
+      }
+    }
+    if (closure && extra != 0.0) {
+      if (diagpos < 0) { scol[m] = r; sval[m] = extra; ++m; }
+      else sval[diagpos] += extra;
+    }
+    sn = m;
+  }
+  __syncthreads();
+  const ST* X = mat + moff[b];
+  RT* Rr = R + soff[e] + (long long)r * ld;
+  float lmax = 0.f;
+  for (int j = threadIdx.x; j < ld; j += blockDim.x) {
+    double acc = (j == r) ? 1.0 : 0.0;
+    if (j < n)
+      for (int k = 0; k < sn; ++k) acc -= sval[k] * (double)X[(long long)scol[k] * ld + j];
+    else
+      acc = 0.0;
+    Rr[j] = (RT)acc;
+    lmax = fmaxf(lmax, (float)fabs(acc));
+  }
+  for (int o = 16; o > 0; o >>= 1) lmax = fmaxf(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(rmax + e, __float_as_uint(lmax));
+}
+
+// T = X * R per entry (n x n), 64x64 tiles, K in steps of 64; compute type AT
+template <typename ST, typename RT, typename AT>
+__global__ void k_ns_gemm(const int* __restrict__ lst, const long long* __restrict__ tilepre, int nent,
+                          const int* __restrict__ bn, const int* __restrict__ bld, const long long* __restrict__ moff,
+                          const ST* __restrict__ mat, const long long* __restrict__ soff, const RT* __restrict__ R,
+                          AT* __restrict__ Tout) {
+  extern __shared__ unsigned char smraw[];
+  AT(*As)[TB + 1] = (AT(*)[TB + 1])smraw;
+  AT(*Bs)[TB + 1] = (AT(*)[TB + 1])(smraw + sizeof(AT) * TB * (TB + 1));
+  long long w = blockIdx.x;
+  int e = find_block(tilepre, nent, w);
+  int b = lst[e];
+  int n = bn[b], ld = bld[b];
+  int T = (n + TB - 1) / TB;
+  long long loc = w - tilepre[e];
+  int it = (int)(loc / T), jt = (int)(loc % T);
+  int i0 = it * TB, j0 = jt * TB;
+  const ST* X = mat + moff[b];
+  const RT* Rm = R + soff[e];
+  int ty = threadIdx.x / 16, tx = threadIdx.x % 16;
+  AT acc[4][4] = {};
+  for (int k0 = 0; k0 < n; k0 += TB) {
+    __syncthreads();
+    for (int q = threadIdx.x; q < TB * TB; q += blockDim.x) {
+      int i = q / TB, j = q % TB;
+      As[i][j] = (i0 + i < n && k0 + j < n) ? (AT)X[(long long)(i0 + i) * ld + k0 + j] : (AT)0;
+      Bs[i][j] = (k0 + i < n && j0 + j < n) ? (AT)Rm[(long long)(k0 + i) * ld + j0 + j] : (AT)0;
+    }
+    __syncthreads();
+    for (int kk = 0; kk < TB; ++kk) {
+      AT a[4], bb[4];
+      for (int i = 0; i < 4; ++i) a[i] = As[ty * 4 + i][kk];
+      for (int j = 0; j < 4; ++j) bb[j] = Bs[kk][tx * 4 + j];
+      for (int i = 0; i < 4; ++i)
+        for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * bb[j];
+    }
+  }
+  AT* To = Tout + soff[e];
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) {
+      int r = i0 + ty * 4 + i, c = j0 + tx * 4 + j;
+      if (r < n && c < n) To[(long long)r * ld + c] = acc[i][j];
+    }
+}
+
+// X += T for every entry (flat over n*ld elements of each entry)
+template <typename ST, typename AT>
+__global__ void k_ns_add(const int* __restrict__ lst, const long long* __restrict__ elpre, int nent,
+                         const int* __restrict__ bn, const int* __restrict__ bld, const long long* __restrict__ moff,
+                         ST* __restrict__ mat, const long long* __restrict__ soff, const AT* __restrict__ T) {
+  long long w = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (w >= elpre[nent]) return;
+  int e = find_block(elpre, nent, w);
+  int b = lst[e];
+  long long loc = w - elpre[e];
+  int ld = bld[b];
+  int r = (int)(loc / ld), c = (int)(loc % ld);
+  if (r >= bn[b] || c >= bn[b]) return;
+  ST* x = mat + moff[b] + loc;
+  *x = (ST)((AT)*x + T[soff[e] + loc]);
+}
+
+// closure-block residual for the basis solves: res = rhs - Abar * S (FP64, n x kc per block)
+__global__ void k_closure_residual(Geo G, Phy P, const uint8_t* __restrict__ fl, int op, const double* __restrict__ st,
+                                   const int* __restrict__ owner, int nblk, const long long* __restrict__ ioff,
+                                   const int* __restrict__ bn, const int* __restrict__ idx, long long n_total,
+                                   const long long* __restrict__ roff, const int* __restrict__ kcv,
+                                   const double* __restrict__ rhs, const double* __restrict__ S,
+                                   double* __restrict__ res) {
+  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= n_total) return;
+  int b = find_block(ioff, nblk, t);
+  int r = (int)(t - ioff[b]);
+  int n = bn[b];
+  if (r >= n) return;
+  const int* bidx = idx + ioff[b];
+  int g = bidx[r];
+  int kc = kcv[b];
+  RowList L;
+  L.n = 0;
+  any_row<double>(G, P, fl, op, st, g, L);
+  int me = owner[g];
+  const double* Sb = S + roff[b];
+  double* out = res + roff[b] + (long long)r * kc;
+  const double* in = rhs + roff[b] + (long long)r * kc;
+  for (int q = 0; q < kc; ++q) out[q] = in[q];
+  double extra = 0.0;
+  for (int k = 0; k < L.n; ++k) {
+    int lc = lower_idx(bidx, n, L.col[k]);
+    if (lc < n && bidx[lc] == L.col[k]) {
+      for (int q = 0; q < kc; ++q) out[q] -= L.val[k] * Sb[(long long)lc * kc + q];
+    } else {
+      int o = owner[L.col[k]];
+      if (o == -3 || (o >= 0 && o != me)) extra += L.val[k];
+    }
+  }
+  if (extra != 0.0)
+    for (int q = 0; q < kc; ++q) out[q] -= extra * Sb[(long long)r * kc + q];
+}
+
+__global__ void k_add_vec(double* __restrict__ a, const double* __restrict__ b, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    a[i] += b[i];
+}
+
+}  // namespace
+
+// ================================================================================ launchers
+template <typename ST>
+cudaError_t launch_assemble(const Ctx& C, const BlockSet& B, int op, const double* state, ST* mat, int closure) {
+  if (B.nblk == 0) return cudaSuccess;
+  int thr = 128;
+  long long blk = (B.n_total + thr - 1) / thr;
+  k_assemble<ST><<<(unsigned)blk, thr, 0, C.stream>>>(C.G, C.P, C.flags.as<uint8_t>(), op, state, C.owner.as<int>(),
+                                                      B.nblk, B.d_ioff.as<long long>(), B.d_n.as<int>(),
+                                                      B.d_ld.as<int>(), B.d_moff.as<long long>(), B.idx.as<int>(),
+                                                      B.n_total, mat, closure);
+  return cudaGetLastError();
+}
+template cudaError_t launch_assemble<double>(const Ctx&, const BlockSet&, int, const double*, double*, int);
+template cudaError_t launch_assemble<float>(const Ctx&, const BlockSet&, int, const double*, float*, int);
+
+template <typename ST>
+cudaError_t launch_gj_invert(const BlockSet& B, ST* mat, int* d_bad, cudaStream_t s) {
+  if (B.nblk == 0) return cudaSuccess;
+  // order blocks by tile count (descending): the active set at step k is a prefix
+  std::vector<int> order(B.nblk);
+  for (int i = 0; i < B.nblk; ++i) order[i] = i;
+  std::vector<int> T(B.nblk);
+  for (int i = 0; i < B.nblk; ++i) T[i] = (B.n[i] + TB - 1) / TB;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return T[a] > T[b]; });
+  std::vector<long long> pre1(B.nblk + 1, 0), pre2(B.nblk + 1, 0);
+  for (int s2 = 0; s2 < B.nblk; ++s2) {
+    long long t = T[order[s2]] - 1;
+    pre1[s2 + 1] = pre1[s2] + t;
+    pre2[s2 + 1] = pre2[s2] + t * t;
+  }
+  int *d_order = nullptr;
+  long long *d_pre1 = nullptr, *d_pre2 = nullptr;
+  cudaError_t e;
+  if ((e = cudaMalloc(&d_order, sizeof(int) * B.nblk)) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&d_pre1, sizeof(long long) * (B.nblk + 1))) != cudaSuccess) { cudaFree(d_order); return e; }
+  if ((e = cudaMalloc(&d_pre2, sizeof(long long) * (B.nblk + 1))) != cudaSuccess) {
+    cudaFree(d_order); cudaFree(d_pre1); return e;
+  }
+  cudaMemcpyAsync(d_order, order.data(), sizeof(int) * B.nblk, cudaMemcpyHostToDevice, s);
+  cudaMemcpyAsync(d_pre1, pre1.data(), sizeof(long long) * (B.nblk + 1), cudaMemcpyHostToDevice, s);
+  cudaMemcpyAsync(d_pre2, pre2.data(), sizeof(long long) * (B.nblk + 1), cudaMemcpyHostToDevice, s);
+  size_t smem = 2 * sizeof(ST) * TB * (TB + 1);
+  cudaFuncSetAttribute(k_gj_rowpanel<ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaFuncSetAttribute(k_gj_update<ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaFuncSetAttribute(k_gj_colpanel<ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int Tmax = T[order[0]];
+  int cnt = B.nblk;
+  for (int k = 0; k < Tmax; ++k) {
+    while (cnt > 0 && T[order[cnt - 1]] <= k) --cnt;
+    k_gj_diag<ST><<<cnt, 256, 0, s>>>(k, d_order, B.d_n.as<int>(), B.d_ld.as<int>(), B.d_moff.as<long long>(), mat,
+                                      d_bad);
+    if (pre1[cnt] > 0) {
+      k_gj_rowpanel<ST><<<(unsigned)pre1[cnt], 256, smem, s>>>(k, cnt, d_order, d_pre1, B.d_n.as<int>(),
+                                                               B.d_ld.as<int>(), B.d_moff.as<long long>(), mat);
+      if (pre2[cnt] > 0)
+        k_gj_update<ST><<<(unsigned)pre2[cnt], 256, smem, s>>>(k, cnt, d_order, d_pre2, B.d_n.as<int>(),
+                                                               B.d_ld.as<int>(), B.d_moff.as<long long>(), mat);
+      k_gj_colpanel<ST><<<(unsigned)pre1[cnt], 256, smem, s>>>(k, cnt, d_order, d_pre1, B.d_n.as<int>(),
+                                                               B.d_ld.as<int>(), B.d_moff.as<long long>(), mat);
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess) break;
+  }
+  cudaStreamSynchronize(s);
+  cudaFree(d_order);
+  cudaFree(d_pre1);
+  cudaFree(d_pre2);
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+template cudaError_t launch_gj_invert<double>(const BlockSet&, double*, int*, cudaStream_t);
+template cudaError_t launch_gj_invert<float>(const BlockSet&, float*, int*, cudaStream_t);
+
+cudaError_t launch_closure_rhs(const Ctx& C, const BlockSet& B, int op, const double* state, const int* d_colbase,
+                               const int* d_cols, const long long* d_roff, const int* d_kc, double* rhs) {
+  if (B.nblk == 0) return cudaSuccess;
+  int thr = 128;
+  long long blk = (B.n_total + thr - 1) / thr;
+  k_closure_rhs<<<(unsigned)blk, thr, 0, C.stream>>>(C.G, C.P, C.flags.as<uint8_t>(), op, state,
+                                                     C.cell_iface.as<int>(), B.nblk, B.d_ioff.as<long long>(),
+                                                     B.d_n.as<int>(), B.idx.as<int>(), B.n_total, d_colbase, d_cols,
+                                                     d_roff, d_kc, rhs);
+  return cudaGetLastError();
+}
+
+template <typename ST, typename AT>
+cudaError_t launch_block_mm(const BlockSet& B, const ST* mat, const double* rhs, const long long* d_roff,
+                            const int* d_kc, double* out, cudaStream_t s) {
+  if (B.nblk == 0) return cudaSuccess;
+  long long warps = B.n_total;
+  long long blk = (warps * 32 + 255) / 256;
+  k_block_mm<ST, AT><<<(unsigned)blk, 256, 0, s>>>(B.nblk, B.d_ioff.as<long long>(), B.d_n.as<int>(),
+                                                   B.d_ld.as<int>(), B.d_moff.as<long long>(), mat, B.n_total, rhs,
+                                                   d_roff, d_kc, out);
+  return cudaGetLastError();
+}
+template cudaError_t launch_block_mm<double, double>(const BlockSet&, const double*, const double*, const long long*,
+                                                     const int*, double*, cudaStream_t);
+template cudaError_t launch_block_mm<float, float>(const BlockSet&, const float*, const double*, const long long*,
+                                                   const int*, double*, cudaStream_t);
+
+template <typename ST, typename PT>
+cudaError_t launch_local_solve(const BlockSet& B, const ST* mat, const double* t, double* z, PT* pk_x, int add,
+                               cudaStream_t s) {
+  if (B.nblk == 0) return cudaSuccess;
+  int thr = 256;
+  long long blk = (B.n_total + thr - 1) / thr;
+  k_gather<PT><<<(unsigned)blk, thr, 0, s>>>(B.idx.as<int>(), B.n_total, t, pk_x);
+  k_local_gemv<ST, PT><<<B.nitems, 256, 0, s>>>(B.items.as<int4>(), B.idx.as<int>(), B.d_ioff.as<long long>(),
+                                                B.d_ld.as<int>(), B.d_moff.as<long long>(), mat, pk_x, z, add);
+  return cudaGetLastError();
+}
+template cudaError_t launch_local_solve<double, double>(const BlockSet&, const double*, const double*, double*,
+                                                        double*, int, cudaStream_t);
+template cudaError_t launch_local_solve<float, float>(const BlockSet&, const float*, const double*, double*, float*,
+                                                      int, cudaStream_t);
+template cudaError_t launch_local_solve<__nv_bfloat16, float>(const BlockSet&, const __nv_bfloat16*, const double*,
+                                                              double*, float*, int, cudaStream_t);
+
+// Refine the inverses of a block set: blocks whose max |I - A X| exceeds `thresh` get `steps`
+// Newton-Schulz steps.  Scratch is bounded by `budget_bytes` (blocks processed in chunks).
+template <typename ST, typename AT>
+cudaError_t launch_ns_refine(const Ctx& C, const BlockSet& B, int op, const double* state, int closure, ST* mat,
+                             int steps, double thresh, size_t budget_bytes, double* max_before, double* max_after) {
+  if (B.nblk == 0 || steps <= 0) return cudaSuccess;
+  cudaStream_t s = C.stream;
+  cudaError_t e = cudaSuccess;
+  *max_before = 0;
+  if (max_after) *max_after = 0;
+  size_t smem = 2 * sizeof(AT) * TB * (TB + 1);
+  cudaFuncSetAttribute(k_ns_gemm<ST, AT, AT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  // chunks of consecutive blocks whose R and T fit the budget
+  int b0 = 0;
+  while (b0 < B.nblk && e == cudaSuccess) {
+    std::vector<int> lst;
+    std::vector<long long> soff(1, 0);
+    size_t used = 0;
+    int b = b0;
+    while (b < B.nblk) {
+      size_t need = 2 * sizeof(AT) * (size_t)B.ld[b] * B.ld[b];
+      if (!lst.empty() && used + need > budget_bytes) break;
+      lst.push_back(b);
+      used += need;
+      soff.push_back(soff.back() + (long long)B.ld[b] * B.ld[b]);
+      ++b;
+    }
+    b0 = b;
+    int nent = (int)lst.size();
+    std::vector<double> prev(nent, 1e300);
+    for (int step = 0; step < steps && e == cudaSuccess; ++step) {
+      std::vector<long long> rowpre(nent + 1, 0);
+      for (int q = 0; q < nent; ++q) rowpre[q + 1] = rowpre[q] + B.n[lst[q]];
+      int *d_lst = nullptr;
+      long long *d_pre = nullptr, *d_soff = nullptr;
+      unsigned int* d_rmax = nullptr;
+      AT *R = nullptr, *T = nullptr;
+      if ((e = cudaMalloc(&d_lst, sizeof(int) * nent)) != cudaSuccess) break;
+      cudaMalloc(&d_pre, sizeof(long long) * (nent + 1));
+      cudaMalloc(&d_soff, sizeof(long long) * (nent + 1));
+      cudaMalloc(&d_rmax, sizeof(unsigned int) * nent);
+      if ((e = cudaMalloc(&R, sizeof(AT) * soff[nent])) != cudaSuccess) { cudaFree(d_lst); break; }
+      if ((e = cudaMalloc(&T, sizeof(AT) * soff[nent])) != cudaSuccess) { cudaFree(d_lst); cudaFree(R); break; }
+      cudaMemcpyAsync(d_lst, lst.data(), sizeof(int) * nent, cudaMemcpyHostToDevice, s);
+      cudaMemcpyAsync(d_pre, rowpre.data(), sizeof(long long) * (nent + 1), cudaMemcpyHostToDevice, s);
+      cudaMemcpyAsync(d_soff, soff.data(), sizeof(long long) * (nent + 1), cudaMemcpyHostToDevice, s);
+      cudaMemsetAsync(d_rmax, 0, sizeof(unsigned int) * nent, s);
+      cudaMemsetAsync(R, 0, sizeof(AT) * soff[nent], s);
+      k_ns_residual<ST, AT><<<(unsigned)rowpre[nent], 256, 0, s>>>(
+          C.G, C.P, C.flags.as<uint8_t>(), op, state, C.owner.as<int>(), closure, d_lst, d_pre, nent,
+          B.d_ioff.as<long long>(), B.d_n.as<int>(), B.d_ld.as<int>(), B.d_moff.as<long long>(), B.idx.as<int>(), mat,
+          d_soff, R, d_rmax);
+      std::vector<unsigned int> rm(nent);
+      cudaMemcpyAsync(rm.data(), d_rmax, sizeof(unsigned int) * nent, cudaMemcpyDeviceToHost, s);
+      e = cudaStreamSynchronize(s);
+      // refine only the blocks above the threshold
+      std::vector<int> sel;
+      std::vector<long long> ssoff;
+      for (int q = 0; q < nent; ++q) {
+        float v;
+        memcpy(&v, &rm[q], sizeof v);
+        if (step == 0) *max_before = std::max(*max_before, (double)v);
+        // refine while the residual is above the floor and still falls fast (quadratic phase);
+        // once it stalls it sits at the storage-rounding floor cond * eps and further steps are moot
+        // a step from |I - A X| >= 1/2 would not contract (and diverges beyond 1): leave such blocks
+        bool go = v > thresh && v < 0.5f && (step == 0 || v < 0.25 * prev[q]);
+        prev[q] = v;
+        if (go) { sel.push_back(lst[q]); ssoff.push_back(soff[q]); }
+      }
+      if (e == cudaSuccess && !sel.empty()) {
+        int ns = (int)sel.size();
+        std::vector<long long> tpre(ns + 1, 0), epre(ns + 1, 0);
+        for (int q = 0; q < ns; ++q) {
+          long long Tt = (B.n[sel[q]] + TB - 1) / TB;
+          tpre[q + 1] = tpre[q] + Tt * Tt;
+          epre[q + 1] = epre[q] + (long long)B.ld[sel[q]] * B.ld[sel[q]];
+        }
+        ssoff.push_back(0);
+        int* d_sel = nullptr;
+        long long *d_tpre = nullptr, *d_epre = nullptr, *d_ssoff = nullptr;
+        cudaMalloc(&d_sel, sizeof(int) * ns);
+        cudaMalloc(&d_tpre, sizeof(long long) * (ns + 1));
+        cudaMalloc(&d_epre, sizeof(long long) * (ns + 1));
+        cudaMalloc(&d_ssoff, sizeof(long long) * (ns + 1));
+        cudaMemcpyAsync(d_sel, sel.data(), sizeof(int) * ns, cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(d_tpre, tpre.data(), sizeof(long long) * (ns + 1), cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(d_epre, epre.data(), sizeof(long long) * (ns + 1), cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(d_ssoff, ssoff.data(), sizeof(long long) * (ns + 1), cudaMemcpyHostToDevice, s);
+        k_ns_gemm<ST, AT, AT><<<(unsigned)tpre[ns], 256, smem, s>>>(d_sel, d_tpre, ns, B.d_n.as<int>(),
+                                                                   B.d_ld.as<int>(), B.d_moff.as<long long>(), mat,
+                                                                   d_ssoff, R, T);
+        k_ns_add<ST, AT><<<(unsigned)((epre[ns] + 255) / 256), 256, 0, s>>>(
+            d_sel, d_epre, ns, B.d_n.as<int>(), B.d_ld.as<int>(), B.d_moff.as<long long>(), mat, d_ssoff, T);
+        e = cudaStreamSynchronize(s);
+        if (e == cudaSuccess) e = cudaGetLastError();
+        cudaFree(d_sel);
+        cudaFree(d_tpre);
+        cudaFree(d_epre);
+        cudaFree(d_ssoff);
+      }
+      cudaFree(d_lst);
+      cudaFree(d_pre);
+      cudaFree(d_soff);
+      cudaFree(d_rmax);
+      cudaFree(R);
+      cudaFree(T);
+      if (sel.empty()) break;
+    }
+  }
+  // final residual of every block (report, only when asked for)
+  if (e == cudaSuccess && max_after) {
+    int nent = B.nblk;
+    std::vector<int> lst(nent);
+    std::vector<long long> rowpre(nent + 1, 0), soff(nent + 1, 0);
+    size_t maxm = 0;
+    for (int q = 0; q < nent; ++q) {
+      lst[q] = q;
+      rowpre[q + 1] = rowpre[q] + B.n[q];
+      maxm = std::max(maxm, (size_t)B.ld[q] * B.ld[q]);
+    }
+    // one block at a time through a single scratch slot, residual max only
+    AT* R = nullptr;
+    int* d_lst = nullptr;
+    long long *d_pre = nullptr, *d_soff = nullptr;
+    unsigned int* d_rmax = nullptr;
+    if ((e = cudaMalloc(&R, sizeof(AT) * maxm)) == cudaSuccess) {
+      cudaMalloc(&d_lst, sizeof(int));
+      cudaMalloc(&d_pre, sizeof(long long) * 2);
+      cudaMalloc(&d_soff, sizeof(long long) * 2);
+      cudaMalloc(&d_rmax, sizeof(unsigned int));
+      long long zero2[2] = {0, 0};
+      cudaMemcpyAsync(d_soff, zero2, sizeof zero2, cudaMemcpyHostToDevice, s);
+      for (int q = 0; q < nent && e == cudaSuccess; ++q) {
+        long long pre[2] = {0, B.n[q]};
+        cudaMemcpyAsync(d_lst, &q, sizeof(int), cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(d_pre, pre, sizeof pre, cudaMemcpyHostToDevice, s);
+        cudaMemsetAsync(d_rmax, 0, sizeof(unsigned int), s);
+        k_ns_residual<ST, AT><<<(unsigned)B.n[q], 256, 0, s>>>(
+            C.G, C.P, C.flags.as<uint8_t>(), op, state, C.owner.as<int>(), closure, d_lst, d_pre, 1,
+            B.d_ioff.as<long long>(), B.d_n.as<int>(), B.d_ld.as<int>(), B.d_moff.as<long long>(), B.idx.as<int>(),
+            mat, d_soff, R, d_rmax);
+        unsigned int rmv = 0;
+        cudaMemcpyAsync(&rmv, d_rmax, sizeof rmv, cudaMemcpyDeviceToHost, s);
+        e = cudaStreamSynchronize(s);
+        float v;
+        memcpy(&v, &rmv, sizeof v);
+        *max_after = std::max(*max_after, (double)v);
+      }
+      cudaFree(d_lst);
+      cudaFree(d_pre);
+      cudaFree(d_soff);
+      cudaFree(d_rmax);
+      cudaFree(R);
+    }
+  }
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+template cudaError_t launch_ns_refine<float, float>(const Ctx&, const BlockSet&, int, const double*, int, float*, int,
+                                                   double, size_t, double*, double*);
+template cudaError_t launch_ns_refine<double, double>(const Ctx&, const BlockSet&, int, const double*, int, double*,
+                                                     int, double, size_t, double*, double*);
+
+cudaError_t launch_closure_residual(const Ctx& C, const BlockSet& B, int op, const double* state,
+                                    const long long* d_roff, const int* d_kc, const double* rhs, const double* S,
+                                    double* res) {
+  if (B.nblk == 0) return cudaSuccess;
+  long long blk = (B.n_total + 127) / 128;
+  k_closure_residual<<<(unsigned)blk, 128, 0, C.stream>>>(C.G, C.P, C.flags.as<uint8_t>(), op, state,
+                                                         C.owner.as<int>(), B.nblk, B.d_ioff.as<long long>(),
+                                                         B.d_n.as<int>(), B.idx.as<int>(), B.n_total, d_roff, d_kc,
+                                                         rhs, S, res);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_add_vec(double* a, const double* b, long long n, cudaStream_t s) {
+  k_add_vec<<<2048, 256, 0, s>>>(a, b, n);
+  return cudaGetLastError();
+}
+
+}  // namespace pns

@@ -1,0 +1,788 @@
+// C ABI of libpns (include/pns.h): context setup, preconditioner build and apply (Secs. 3-4),
+// flexible GMRES and Newton (Sec. 8), the Stokes initial iterate.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "internal.h"
+
+using namespace pns;
+
+struct pns_ctx {
+  Ctx c;
+};
+
+namespace {
+
+constexpr int GEMV_ROWS = 32;   // rows per local-solve work item (8 warps x 4 rows)
+
+int fail(Ctx& C, int code, const char* what, cudaError_t e = cudaSuccess) {
+  char buf[512];
+  if (e != cudaSuccess) snprintf(buf, sizeof buf, "%s: %s", what, cudaGetErrorString(e));
+  else snprintf(buf, sizeof buf, "%s", what);
+  C.err = buf;
+  return code;
+}
+
+#define CK(expr)                                                                                   \
+  do {                                                                                             \
+    cudaError_t e_ = (expr);                                                                       \
+    if (e_ != cudaSuccess)                                                                         \
+      return fail(C, e_ == cudaErrorMemoryAllocation ? PNS_ERR_OOM : PNS_ERR_CUDA, #expr, e_);     \
+  } while (0)
+
+#define CKS(expr)                     \
+  do {                                \
+    int s_ = (expr);                  \
+    if (s_ != PNS_OK) return s_;      \
+  } while (0)
+
+cudaError_t dalloc(DevBuf& b, size_t bytes) {
+  b.release();
+  if (bytes == 0) return cudaSuccess;
+  cudaError_t e = cudaMalloc(&b.p, bytes);
+  if (e == cudaSuccess) b.bytes = bytes;
+  else b.p = nullptr;
+  return e;
+}
+
+template <typename T>
+cudaError_t upload(DevBuf& b, const std::vector<T>& v, cudaStream_t s) {
+  cudaError_t e = dalloc(b, sizeof(T) * std::max<size_t>(v.size(), 1));
+  if (e != cudaSuccess) return e;
+  if (v.empty()) return cudaSuccess;
+  e = cudaMemcpyAsync(b.p, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return e;
+  return cudaStreamSynchronize(s);
+}
+
+double now_ms() {
+  using namespace std::chrono;
+  return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
+}
+
+int vt_bytes(int precision) { return precision == PNS_FP64 ? 8 : 4; }
+int st_bytes(int precision) { return precision == PNS_FP64 ? 8 : (precision == PNS_FP32 ? 4 : 2); }
+
+// --------------------------------------------------------------------------- block sets
+int make_blockset(Ctx& C, BlockSet& B, const std::vector<std::vector<int>>& lists) {
+  B.nblk = (int)lists.size();
+  B.n.resize(B.nblk);
+  B.ld.resize(B.nblk);
+  B.ioff.resize(B.nblk + 1);
+  B.moff.resize(B.nblk + 1);
+  B.n_total = 0;
+  B.m_total = 0;
+  B.sum_n2 = 0;
+  B.nmax = 0;
+  for (int b = 0; b < B.nblk; ++b) {
+    int n = (int)lists[b].size();
+    int np = (n + 7) / 8 * 8;
+    B.n[b] = n;
+    B.ld[b] = np;
+    B.ioff[b] = B.n_total;
+    B.moff[b] = B.m_total;
+    B.n_total += np;
+    B.m_total += (long long)np * np;
+    B.sum_n2 += (double)n * n;
+    B.nmax = std::max(B.nmax, n);
+  }
+  B.ioff[B.nblk] = B.n_total;
+  B.moff[B.nblk] = B.m_total;
+  std::vector<int> idx(B.n_total, -1);
+  std::vector<int4> items;
+  for (int b = 0; b < B.nblk; ++b) {
+    std::copy(lists[b].begin(), lists[b].end(), idx.begin() + B.ioff[b]);
+    for (int r = 0; r < B.n[b]; r += GEMV_ROWS) items.push_back(make_int4(b, r, std::min(GEMV_ROWS, B.n[b] - r), 0));
+  }
+  B.nitems = (int)items.size();
+  std::vector<long long> ioff(B.ioff.begin(), B.ioff.end() - 1), moff(B.moff.begin(), B.moff.end() - 1);
+  if (B.nblk == 0) return PNS_OK;
+  CK(upload(B.idx, idx, C.stream));
+  CK(upload(B.d_n, B.n, C.stream));
+  CK(upload(B.d_ld, B.ld, C.stream));
+  CK(upload(B.d_ioff, ioff, C.stream));
+  CK(upload(B.d_moff, moff, C.stream));
+  CK(upload(B.items, items, C.stream));
+  return PNS_OK;
+}
+
+int op_of_variant(int variant) {
+  switch (variant) {
+    case PNS_APLMM_NS: return OP_NEWTON;
+    case PNS_APLMM_S: return OP_STOKES;
+    default: return OP_OSEEN;
+  }
+}
+
+__global__ void k_f2bf(const float* __restrict__ in, __nv_bfloat16* __restrict__ out, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    out[i] = __float2bfloat16_rn(in[i]);
+}
+__global__ void k_d2f_any(const double* __restrict__ in, float* __restrict__ out, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    out[i] = (float)in[i];
+}
+template <typename VT>
+__global__ void k_sum3(const VT* __restrict__ a, const VT* __restrict__ b, const VT* __restrict__ c,
+                       double* __restrict__ z, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    z[i] = (double)a[i] + (double)b[i] + (double)c[i];
+}
+template <typename VT>
+__global__ void k_from_double(const double* __restrict__ v, VT* __restrict__ out, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    out[i] = (VT)v[i];
+}
+__global__ void k_negate(const double* __restrict__ a, double* __restrict__ b, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    b[i] = -a[i];
+}
+__global__ void k_unit(double* __restrict__ x, int n, int k) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) x[i] = (i == k) ? 1.0 : 0.0;
+}
+__global__ void k_setcol(double* __restrict__ A, int n, int k, const double* __restrict__ col) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) A[(long long)i * n + k] = col[i];
+}
+
+// local inverses of one block set in the storage type of `precision`
+int build_local(Ctx& C, Precond& pc, BlockSet& B, int* d_bad) {
+  if (B.nblk == 0) return PNS_OK;
+  const cudaStream_t s = C.stream;
+  if (pc.precision == PNS_FP64) {
+    CK(dalloc(B.mat, sizeof(double) * B.m_total));
+    CK(cudaMemsetAsync(B.mat.p, 0, B.mat.bytes, s));
+    CK(launch_assemble<double>(C, B, pc.op, pc.state.as<double>(), B.mat.as<double>(), 0));
+    CK(launch_gj_invert<double>(B, B.mat.as<double>(), d_bad, s));
+  } else {
+    DevBuf tmp;
+    DevBuf& F = pc.precision == PNS_FP32 ? B.mat : tmp;
+    CK(dalloc(F, sizeof(float) * B.m_total));
+    CK(cudaMemsetAsync(F.p, 0, F.bytes, s));
+    CK(launch_assemble<float>(C, B, pc.op, pc.state.as<double>(), F.as<float>(), 0));
+    CK(launch_gj_invert<float>(B, F.as<float>(), d_bad, s));
+    // Newton-Schulz refinement with FP64 residuals: the FP32 Gauss-Jordan error (~cond * eps32)
+    // drops to the FP32 rounding of the exact inverse
+    int steps = C.opt.refine_steps >= 0 ? C.opt.refine_steps : 3;
+    if (steps > 0) {
+      size_t fr = 0, tot = 0;
+      cudaMemGetInfo(&fr, &tot);
+      size_t budget = std::max<size_t>(fr / 2, (size_t)1 << 28);
+      double before = 0;
+      CK((launch_ns_refine<float, float>(C, B, pc.op, pc.state.as<double>(), 0, F.as<float>(), steps, 2e-6,
+                                          budget, &before, nullptr)));
+      pc.ns_residual_before = std::max(pc.ns_residual_before, before);
+    }
+    if (pc.precision == PNS_BF16) {
+      CK(dalloc(B.mat, sizeof(__nv_bfloat16) * B.m_total));
+      k_f2bf<<<4096, 256, 0, s>>>(F.as<float>(), B.mat.as<__nv_bfloat16>(), B.m_total);
+      CK(cudaGetLastError());
+      CK(cudaStreamSynchronize(s));
+    }
+  }
+  return PNS_OK;
+}
+
+// restriction segments: interface cells then primary unknowns
+int build_segments(Ctx& C, Precond& pc) {
+  const Maps& M = C.M;
+  std::vector<int> idx;
+  std::vector<long long> off(1, 0);
+  std::vector<int2> items;
+  auto add_seg = [&](const std::vector<int>& list, bool cells) {
+    int sidx = (int)off.size() - 1;
+    for (int v : list) idx.push_back(cells ? C.G.dim * C.G.ncell + v : v);
+    long long len = (long long)list.size();
+    for (long long q = 0; q * 2048 < len; ++q) items.push_back(make_int2(sidx, (int)q));
+    off.push_back((long long)idx.size());
+  };
+  for (int j : M.coarse_ifaces) add_seg(M.iface_cells[j], true);
+  for (int i = 0; i < M.n_prim; ++i) add_seg(M.prim_unk[i], false);
+  pc.nseg_items = (int)items.size();
+  CK(upload(pc.seg_idx, idx, C.stream));
+  CK(upload(pc.seg_off, off, C.stream));
+  CK(upload(pc.seg_items, items, C.stream));
+  return PNS_OK;
+}
+
+// shape/correction vectors (closure blocks, Eqs. 6, 9, 15, 17) and the coarse matrix (Remark 1)
+template <typename SB>
+int build_coarse_t(Ctx& C, Precond& pc, int* d_bad) {
+  const Maps& M = C.M;
+  const cudaStream_t s = C.stream;
+  BlockSet& B = pc.prim;
+  // per-primary RHS layout
+  std::vector<int> kc(M.n_prim), colbase(M.n_prim), cols, colid, coloff(M.n_prim);
+  std::vector<long long> roff(M.n_prim + 1, 0);
+  for (int i = 0; i < M.n_prim; ++i) {
+    kc[i] = (int)M.C[i].size() + 1;
+    colbase[i] = (int)cols.size();
+    coloff[i] = (int)colid.size();
+    for (int j : M.C[i]) { cols.push_back(j); colid.push_back(M.coarse_of_iface[j]); }
+    colid.push_back(pc.n_cif + i);
+    roff[i + 1] = roff[i] + (long long)B.n[i] * kc[i];
+  }
+  pc.kcols = kc;
+  pc.boff.assign(roff.begin(), roff.end() - 1);
+  DevBuf d_kc, d_colbase, d_cols, d_roff;
+  CK(upload(d_kc, kc, s));
+  CK(upload(d_colbase, colbase, s));
+  CK(upload(d_cols, cols, s));
+  std::vector<long long> roffv(roff.begin(), roff.end() - 1);
+  CK(upload(d_roff, roffv, s));
+  CK(upload(pc.d_kcols, kc, s));
+  CK(upload(pc.d_colid, colid, s));
+  CK(upload(pc.d_coloff, coloff, s));
+  CK(upload(pc.d_boff, roffv, s));
+  long long rtot = roff[M.n_prim];
+  DevBuf rhs, out;
+  CK(dalloc(rhs, sizeof(double) * std::max(1LL, rtot)));
+  CK(dalloc(out, sizeof(double) * std::max(1LL, rtot)));
+  CK(cudaMemsetAsync(rhs.p, 0, rhs.bytes, s));
+  CK(launch_closure_rhs(C, B, pc.op, pc.state.as<double>(), d_colbase.as<int>(), d_cols.as<int>(),
+                        d_roff.as<long long>(), d_kc.as<int>(), rhs.as<double>()));
+  {
+    // closure blocks: A_b on p_i plus the row sums of its couplings to f faces and other primary grids
+    DevBuf cm;
+    CK(dalloc(cm, sizeof(SB) * B.m_total));
+    CK(cudaMemsetAsync(cm.p, 0, cm.bytes, s));
+    CK(launch_assemble<SB>(C, B, pc.op, pc.state.as<double>(), cm.as<SB>(), 1));
+    CK(launch_gj_invert<SB>(B, cm.as<SB>(), d_bad, s));
+    CK((launch_block_mm<SB, SB>(B, cm.as<SB>(), rhs.as<double>(), d_roff.as<long long>(), d_kc.as<int>(),
+                                out.as<double>(), s)));
+    // iterative refinement of the shape/correction solves with FP64 residuals of the closure blocks
+    DevBuf res, ds;
+    CK(dalloc(res, sizeof(double) * std::max(1LL, rtot)));
+    CK(dalloc(ds, sizeof(double) * std::max(1LL, rtot)));
+    for (int it = 0; it < 2; ++it) {
+      CK(launch_closure_residual(C, B, pc.op, pc.state.as<double>(), d_roff.as<long long>(), d_kc.as<int>(),
+                                 rhs.as<double>(), out.as<double>(), res.as<double>()));
+      CK((launch_block_mm<SB, SB>(B, cm.as<SB>(), res.as<double>(), d_roff.as<long long>(), d_kc.as<int>(),
+                                  ds.as<double>(), s)));
+      CK(launch_add_vec(out.as<double>(), ds.as<double>(), rtot, s));
+    }
+    CK(cudaStreamSynchronize(s));
+  }
+  // basis in the coarse storage type
+  if (pc.precision == PNS_FP64) {
+    CK(dalloc(pc.basis, sizeof(double) * std::max(1LL, rtot)));
+    CK(cudaMemcpyAsync(pc.basis.p, out.p, sizeof(double) * rtot, cudaMemcpyDeviceToDevice, s));
+  } else {
+    CK(dalloc(pc.basis, sizeof(float) * std::max(1LL, rtot)));
+    k_d2f_any<<<2048, 256, 0, s>>>(out.as<double>(), pc.basis.as<float>(), rtot);
+    CK(cudaGetLastError());
+  }
+  // coarse matrix A^o = R^ A_b P^ column by column (prolong e_k, apply A_b, restrict)
+  const int no = pc.n_o;
+  DevBuf Ao, ek, zf, yf, col, work, perm;
+  CK(dalloc(Ao, sizeof(double) * (size_t)no * no));
+  CK(dalloc(ek, sizeof(double) * no));
+  CK(dalloc(zf, sizeof(double) * C.nfull));
+  CK(dalloc(yf, sizeof(double) * C.nfull));
+  CK(dalloc(col, sizeof(double) * no));
+  DevBuf zff;
+  if (pc.precision != PNS_FP64) CK(dalloc(zff, sizeof(float) * C.nfull));
+  for (int k = 0; k < no; ++k) {
+    k_unit<<<(no + 255) / 256, 256, 0, s>>>(ek.as<double>(), no, k);
+    if (pc.precision == PNS_FP64) CK((launch_prolong<double, double>(C, pc, ek.as<double>(), zf.as<double>())));
+    else {
+      // the stored FP32 basis column itself (the apply uses the same rounded basis)
+      CK((launch_prolong<float, float>(C, pc, ek.as<double>(), zff.as<float>())));
+      CK(launch_cast_f2d(zff.as<float>(), zf.as<double>(), C.nfull, s));
+    }
+    CK(launch_apply<double>(C, pc.op, pc.state.as<double>(), zf.as<double>(), nullptr, yf.as<double>(), true));
+    CK(launch_seg_sum(pc, yf.p, 1, col.as<double>(), s));
+    k_setcol<<<(no + 255) / 256, 256, 0, s>>>(Ao.as<double>(), no, k, col.as<double>());
+    CK(cudaGetLastError());
+  }
+  CK(dalloc(work, sizeof(double) * no));
+  CK(dalloc(perm, sizeof(int) * no));
+  CK(launch_coarse_invert(Ao.as<double>(), no, work.as<double>(), perm.as<int>(), d_bad, s));
+  // the coarse inverse stays FP64 in every precision: it is small (N_o^2 entries) and the coarse
+  // matrix can be ill-conditioned (cond ~1e8 on a 96^3 sphere pack), which FP32 storage would ruin
+  pc.ao_inv.release();
+  pc.ao_inv.p = Ao.p;
+  pc.ao_inv.bytes = Ao.bytes;
+  Ao.p = nullptr;
+  Ao.bytes = 0;
+  CK(cudaStreamSynchronize(s));
+  return PNS_OK;
+}
+
+int ensure_scratch(Ctx& C, const Precond& pc) {
+  const int precision = pc.precision;
+  size_t vb = sizeof(double) * C.nfull;
+  DevBuf* ws[5] = {&C.w0, &C.w1, &C.w2, &C.w3, &C.w4};
+  for (DevBuf* w : ws)
+    if (w->bytes < vb) CK(dalloc(*w, vb));
+  long long pk = std::max(pc.prim.n_total, pc.dual.n_total);
+  size_t pb = (size_t)vt_bytes(precision) * std::max(1LL, pk);
+  if (C.pk_x.bytes < pb) CK(dalloc(C.pk_x, pb));
+  size_t cb = sizeof(double) * std::max(1, pc.n_o);
+  if (C.coarse_rhs.bytes < cb) CK(dalloc(C.coarse_rhs, cb));
+  if (C.coarse_x.bytes < cb) CK(dalloc(C.coarse_x, cb));
+  return PNS_OK;
+}
+
+int build_precond(Ctx& C, Precond& pc, int variant, const double* x_lin) {
+  const cudaStream_t s = C.stream;
+  pc.built = false;
+  pc.variant = variant;
+  pc.precision = C.opt.precision;
+  pc.op = op_of_variant(variant);
+  pc.coarse = variant != PNS_ML_ONLY;
+  pc.n_cif = (int)C.M.coarse_ifaces.size();
+  pc.n_o = pc.n_cif + C.M.n_prim;
+  CK(dalloc(pc.state, sizeof(double) * C.nfull));
+  if (x_lin) CK(cudaMemcpyAsync(pc.state.p, x_lin, sizeof(double) * C.nfull, cudaMemcpyDeviceToDevice, s));
+  else CK(cudaMemsetAsync(pc.state.p, 0, sizeof(double) * C.nfull, s));
+  if (pc.prim.nblk != C.M.n_prim || pc.prim.idx.p == nullptr) CKS(make_blockset(C, pc.prim, C.M.prim_unk));
+  if (pc.dual.nblk != C.M.n_iface || (C.M.n_iface && pc.dual.idx.p == nullptr)) CKS(make_blockset(C, pc.dual, C.M.dual_unk));
+  CKS(build_segments(C, pc));
+  DevBuf bad;
+  CK(dalloc(bad, sizeof(int)));
+  CK(cudaMemsetAsync(bad.p, 0, sizeof(int), s));
+  double t0 = now_ms();
+  CKS(build_local(C, pc, pc.prim, bad.as<int>()));
+  CKS(build_local(C, pc, pc.dual, bad.as<int>()));
+  CK(cudaStreamSynchronize(s));
+  double t1 = now_ms();
+  C.t_ml_ms = t1 - t0;
+  if (pc.coarse) {
+    if (pc.precision == PNS_FP64) CKS(build_coarse_t<double>(C, pc, bad.as<int>()));
+    else CKS(build_coarse_t<float>(C, pc, bad.as<int>()));
+  }
+  C.t_mg_ms = now_ms() - t1;
+  int hbad = 0;
+  CK(cudaMemcpy(&hbad, bad.p, sizeof(int), cudaMemcpyDeviceToHost));
+  if (hbad) return fail(C, PNS_ERR_SINGULAR, "zero or non-finite pivot in a local or coarse factor");
+  pc.local_bytes = 0;
+  for (BlockSet* B : {&pc.prim, &pc.dual})
+    for (int b = 0; b < B->nblk; ++b)
+      pc.local_bytes += (double)B->n[b] * B->ld[b] * st_bytes(pc.precision) +   // inverse
+                        8.0 * B->n[b] + 8.0 * B->n[b] + 4.0 * B->n[b];              // t gather, z write, index
+  CKS(ensure_scratch(C, pc));
+  pc.built = true;
+  return PNS_OK;
+}
+
+template <typename ST, typename PT>
+int local_solve(Ctx& C, Precond& pc, BlockSet& B, const double* t, double* z, int add) {
+  (void)pc;
+  if (C.opt.timing) cudaEventRecord(C.ev0, C.stream);
+  CK((launch_local_solve<ST, PT>(B, B.mat.as<ST>(), t, z, C.pk_x.as<PT>(), add, C.stream)));
+  if (C.opt.timing) {
+    cudaEventRecord(C.ev1, C.stream);
+    cudaEventSynchronize(C.ev1);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, C.ev0, C.ev1);
+    C.t_local_ms += ms;
+    C.local_launches += 1;
+  }
+  return PNS_OK;
+}
+
+// z = M^{-1} v.  The local inverses, basis and coarse inverse are stored in the preconditioner's
+// precision and the batched local solves compute in it; the vectors between the stages and the two
+// stencil residual updates (v - A z_G, t - A z_d) are FP64: those differences cancel strongly when
+// z_G is large (ill-conditioned coarse systems), and in FP32 their error would scale with |A z_G|.
+int precond_apply_impl(Ctx& C, Precond& pc, const double* v, double* z) {
+  const cudaStream_t s = C.stream;
+  const long long n = C.nfull;
+  double *zG = C.w1.as<double>(), *t1 = C.w2.as<double>(), *zd = C.w3.as<double>(), *t2 = C.w4.as<double>();
+  double* zp = C.w0.as<double>();
+  int op = pc.op;
+  const double* st = pc.state.as<double>();
+  if (C.opt.combine == PNS_COMBINE_CURRENT && C.cur_state) {
+    op = OP_NEWTON;
+    st = C.cur_state;
+  }
+  if (pc.coarse) {
+    CK(launch_seg_sum(pc, v, 1, C.coarse_rhs.as<double>(), s));
+    CK(launch_coarse_gemv<double>(pc.ao_inv.as<double>(), pc.n_o, C.coarse_rhs.as<double>(), C.coarse_x.as<double>(), s));
+    if (pc.precision == PNS_FP64) CK((launch_prolong<double, double>(C, pc, C.coarse_x.as<double>(), zG)));
+    else CK((launch_prolong<float, double>(C, pc, C.coarse_x.as<double>(), zG)));
+    CK(launch_apply<double>(C, op, st, zG, v, t1, true));           // t1 = v - A z_G
+  } else {
+    CK(cudaMemsetAsync(zG, 0, sizeof(double) * n, s));
+    CK(cudaMemcpyAsync(t1, v, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  }
+  CK(cudaMemsetAsync(zd, 0, sizeof(double) * n, s));
+  if (pc.precision == PNS_FP64) CKS((local_solve<double, double>(C, pc, pc.dual, t1, zd, 1)));
+  else if (pc.precision == PNS_FP32) CKS((local_solve<float, float>(C, pc, pc.dual, t1, zd, 1)));
+  else CKS((local_solve<__nv_bfloat16, float>(C, pc, pc.dual, t1, zd, 1)));
+  CK(launch_apply<double>(C, op, st, zd, t1, t2, true));             // t2 = t1 - A z_d
+  CK(cudaMemsetAsync(zp, 0, sizeof(double) * n, s));
+  if (pc.precision == PNS_FP64) CKS((local_solve<double, double>(C, pc, pc.prim, t2, zp, 0)));
+  else if (pc.precision == PNS_FP32) CKS((local_solve<float, float>(C, pc, pc.prim, t2, zp, 0)));
+  else CKS((local_solve<__nv_bfloat16, float>(C, pc, pc.prim, t2, zp, 0)));
+  k_sum3<double><<<2048, 256, 0, s>>>(zG, zd, zp, z, n);
+  CK(cudaGetLastError());
+  return PNS_OK;
+}
+
+int precond_apply(Ctx& C, Precond& pc, const double* v, double* z) {
+  if (!pc.built) return fail(C, PNS_ERR_STATE, "preconditioner not built");
+  return precond_apply_impl(C, pc, v, z);
+}
+
+// --------------------------------------------------------------------------- Krylov
+int ensure_krylov(Ctx& C, int m) {
+  if (C.m_alloc >= m) return PNS_OK;
+  CK(dalloc(C.V, sizeof(double) * (size_t)(m + 1) * C.nfull));
+  CK(dalloc(C.Z, sizeof(double) * (size_t)m * C.nfull));
+  CK(dalloc(C.H, sizeof(double) * (size_t)(m + 1) * m));
+  CK(dalloc(C.givens, sizeof(double) * (3 * (m + 1) + 8)));
+  CK(dalloc(C.hvec, sizeof(double) * 4 * (m + 1)));
+  CK(dalloc(C.partial, sizeof(double) * 1024 * (m + 2)));
+  C.m_alloc = m;
+  return PNS_OK;
+}
+
+double host_norm(Ctx& C, const double* a, int& st) {
+  double* out = C.hvec.as<double>() + 3 * (C.m_alloc + 1);
+  cudaError_t e = launch_dot(a, a, C.nfull, C.partial.as<double>(), out, C.stream);
+  double h = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, out, sizeof(double), cudaMemcpyDeviceToHost, C.stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(C.stream);
+  st = e == cudaSuccess ? PNS_OK : fail(C, PNS_ERR_CUDA, "norm", e);
+  return std::sqrt(h);
+}
+
+// Solve J(op, state) dx = b with right-preconditioned FGMRES(m); dx is overwritten.
+int fgmres(Ctx& C, Precond& pc, int op, const double* state, const double* b, double* dx, double tol_abs, int maxit,
+           int& its_out, double& res_out) {
+  const cudaStream_t s = C.stream;
+  const long long n = C.nfull;
+  const int m = std::max(1, C.opt.restart);
+  CKS(ensure_krylov(C, m));
+  double* V = C.V.as<double>();
+  double* Z = C.Z.as<double>();
+  double* H = C.H.as<double>();
+  double* cs = C.givens.as<double>();
+  double* sn = cs + (m + 1);
+  double* g = sn + (m + 1);
+  double* outv = g + (m + 1);
+  double* h1 = C.hvec.as<double>();
+  double* h2 = h1 + (m + 1);
+  double* yv = h2 + (m + 1);
+  double* nrm = yv + (m + 1);
+  CK(cudaMemsetAsync(dx, 0, sizeof(double) * n, s));
+  double* r = V;   // the residual lives in V_0 before normalisation
+  CK(cudaMemcpyAsync(r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  int st = 0;
+  double beta = host_norm(C, r, st);
+  CKS(st);
+  int its = 0;
+  while (beta > tol_abs && its < maxit) {
+    if (!std::isfinite(beta)) return fail(C, PNS_ERR_NAN, "non-finite residual in FGMRES");
+    // V_0 = r / beta ; g = [beta, 0, ...]
+    std::vector<double> gh(m + 1, 0.0);
+    gh[0] = beta;
+    CK(cudaMemcpyAsync(g, gh.data(), sizeof(double) * (m + 1), cudaMemcpyHostToDevice, s));
+    CK(cudaMemsetAsync(H, 0, sizeof(double) * (size_t)(m + 1) * m, s));
+    double binv = 1.0 / beta;
+    CK(cudaMemcpyAsync(nrm, &binv, sizeof(double), cudaMemcpyHostToDevice, s));
+    CK(launch_scale(V, n, nrm, nullptr, 0, s));
+    int k = 0;
+    for (int j = 0; j < m; ++j) {
+      double* vj = V + (size_t)j * n;
+      double* zj = Z + (size_t)j * n;
+      double* w = V + (size_t)(j + 1) * n;
+      CKS(precond_apply(C, pc, vj, zj));
+      CK(launch_apply<double>(C, op, state, zj, nullptr, w, true));
+      // CGS2
+      CK(launch_multidot(V, n, j + 1, w, n, C.partial.as<double>(), 0, h1, s));
+      CK(launch_multi_axpy(w, V, n, j + 1, h1, -1.0, n, s));
+      CK(launch_multidot(V, n, j + 1, w, n, C.partial.as<double>(), 0, h2, s));
+      CK(launch_multi_axpy(w, V, n, j + 1, h2, -1.0, n, s));
+      CK(launch_dot(w, w, n, C.partial.as<double>(), nrm, s));
+      CK(launch_hcol(H, m, j, h1, h2, nrm, s));
+      CK(launch_scale(w, n, nullptr, nrm, 1, s));
+      CK(launch_givens(H, m, cs, sn, g, j, outv, s));
+      double hres[2];
+      CK(cudaMemcpyAsync(hres, outv, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      ++its;
+      k = j + 1;
+      if (!std::isfinite(hres[0])) return fail(C, PNS_ERR_NAN, "non-finite Givens residual");
+      res_out = hres[0];
+      if (hres[0] <= tol_abs || its >= maxit) break;
+    }
+    CK(launch_trisolve_update(H, m, g, k, yv, Z, n, dx, n, s));
+    // true residual for the restart: r = b - J dx
+    CK(launch_apply<double>(C, op, state, dx, b, r, true));
+    beta = host_norm(C, r, st);
+    CKS(st);
+    res_out = beta;
+  }
+  its_out = its;
+  return PNS_OK;
+}
+
+int newton(Ctx& C, Precond& pc, int stokes, double* x, const double* x_prev, pns_stats* stt) {
+  const cudaStream_t s = C.stream;
+  const long long n = C.nfull;
+  CK(dalloc(C.rk, sizeof(double) * n));
+  CK(dalloc(C.dx, sizeof(double) * n));
+  CK(dalloc(C.xk, sizeof(double) * n));
+  CKS(ensure_krylov(C, std::max(1, C.opt.restart)));
+  // ||r(0)||
+  CK(cudaMemsetAsync(C.xk.p, 0, sizeof(double) * n, s));
+  CK(launch_residual(C, stokes, C.xk.as<double>(), nullptr, C.rk.as<double>()));
+  int st = 0;
+  double r0 = host_norm(C, C.rk.as<double>(), st);
+  CKS(st);
+  if (!(r0 > 0)) r0 = 1.0;
+  pns_stats loc;
+  memset(&loc, 0, sizeof loc);
+  loc.r0_norm = r0;
+  int op = stokes ? OP_STOKES : OP_NEWTON;
+  int maxn = C.opt.max_newton;
+  int code = PNS_OK;
+  double tsol = 0;
+  for (int k = 0;; ++k) {
+    CK(launch_residual(C, stokes, x, x_prev, C.rk.as<double>()));
+    double nr = host_norm(C, C.rk.as<double>(), st);
+    CKS(st);
+    double rel = nr / r0;
+    if (k < 65) loc.res_hist[k] = rel;
+    if (!std::isfinite(rel)) { code = fail(C, PNS_ERR_NAN, "non-finite Newton residual"); break; }
+    if (rel < C.opt.newton_tol) break;
+    if (k >= maxn) { code = fail(C, PNS_ERR_NOT_CONVERGED, "Newton iteration cap reached"); break; }
+    k_negate<<<2048, 256, 0, s>>>(C.rk.as<double>(), C.rk.as<double>(), n);
+    CK(cudaGetLastError());
+    C.cur_state = stokes ? nullptr : x;
+    double t0 = now_ms();
+    int its = 0;
+    double res = 0;
+    int fs = fgmres(C, pc, op, x, C.rk.as<double>(), C.dx.as<double>(), C.opt.inner_tol * r0, C.opt.max_fgmres, its,
+                    res);
+    tsol += now_ms() - t0;
+    if (fs != PNS_OK) { code = fs; break; }
+    if (loc.newton_its < 64) loc.fgmres_its[loc.newton_its] = its;
+    loc.newton_its++;
+    loc.fgmres_its_total += its;
+    CK(launch_axpy(x, C.dx.as<double>(), 1.0, n, s));
+  }
+  C.cur_state = nullptr;
+  CK(cudaStreamSynchronize(s));
+  loc.t_sol_ms = tsol;
+  loc.t_setup_ms = C.t_setup_ms;
+  loc.t_mg_ms = C.t_mg_ms;
+  loc.t_ml_ms = C.t_ml_ms;
+  loc.t_local_ms = C.t_local_ms;
+  loc.local_launches = C.local_launches;
+  loc.local_bytes_per_apply = pc.local_bytes;
+  if (stt) *stt = loc;
+  return code;
+}
+
+int check_ctx(const pns_ctx* ctx) { return ctx ? PNS_OK : PNS_ERR_ARG; }
+
+}  // namespace
+
+// ============================================================================ C ABI
+extern "C" {
+
+void pns_default_options(pns_options* o) {
+  if (!o) return;
+  memset(o, 0, sizeof *o);
+  o->periodic[0] = 1;
+  o->variant = PNS_GPLMM;
+  o->precision = PNS_FP64;
+  o->combine = PNS_COMBINE_BUILD;
+  o->n_dilate = 1;
+  o->n_tag = 1;
+  o->restart = 100;
+  o->max_fgmres = 2000;
+  o->max_newton = 30;
+  o->inner_tol = 1e-9;
+  o->newton_tol = 1e-8;
+  o->refine_steps = -1;
+  o->timing = 0;
+  o->stream = nullptr;
+}
+
+int pns_setup(pns_ctx** out, int nz, int ny, int nx, const uint8_t* mask, const int32_t* labels, double rho,
+              double mu, const double b[3], double dt, const pns_options* opt) {
+  if (!out || !mask || !labels || !b || nz < 1 || ny < 1 || nx < 1) return PNS_ERR_ARG;
+  if ((long long)nx * ny * nz * 4 >= (1LL << 31)) return PNS_ERR_ARG;
+  *out = nullptr;
+  pns_ctx* ctx = new (std::nothrow) pns_ctx;
+  if (!ctx) return PNS_ERR_OOM;
+  Ctx& C = ctx->c;
+  double t0 = now_ms();
+  if (opt) C.opt = *opt;
+  else pns_default_options(&C.opt);
+  if (C.opt.restart < 1 || C.opt.restart > 127 || C.opt.n_dilate < 0 || C.opt.n_tag < 1 || C.opt.precision < 0 ||
+      C.opt.precision > 2 || C.opt.variant < 0 || C.opt.variant > 3) {
+    delete ctx;
+    return PNS_ERR_ARG;
+  }
+  if (!(rho > 0) || !(mu > 0)) {
+    delete ctx;
+    return PNS_ERR_ARG;
+  }
+  C.stream = (cudaStream_t)C.opt.stream;
+  C.G.nx = nx;
+  C.G.ny = ny;
+  C.G.nz = nz;
+  C.G.dim = nz == 1 ? 2 : 3;
+  C.G.ncell = nx * ny * nz;
+  for (int a = 0; a < 3; ++a) C.G.per[a] = C.opt.periodic[a] ? 1 : 0;
+  if (C.G.dim == 2) C.G.per[2] = 0;
+  C.P.rho = rho;
+  C.P.mu = mu;
+  C.P.inv_dt = dt > 0 ? 1.0 / dt : 0.0;
+  for (int a = 0; a < 3; ++a) C.P.b[a] = b[a];
+  C.nfull = (long long)(C.G.dim + 1) * C.G.ncell;
+  int rc = build_maps(C.G, mask, labels, C.opt.n_dilate, C.opt.n_tag, C.M, C.err);
+  if (rc != 0) {
+    delete ctx;
+    return PNS_ERR_ARG;
+  }
+  int st = PNS_OK;
+  do {
+    cudaError_t e;
+    if ((e = upload(C.flags, C.M.flags, C.stream)) != cudaSuccess) { st = fail(C, PNS_ERR_CUDA, "upload flags", e); break; }
+    if ((e = upload(C.owner, C.M.owner, C.stream)) != cudaSuccess) { st = fail(C, PNS_ERR_CUDA, "upload owner", e); break; }
+    if ((e = upload(C.cell_iface, C.M.cell_iface, C.stream)) != cudaSuccess) { st = fail(C, PNS_ERR_CUDA, "upload iface", e); break; }
+    if ((e = cudaEventCreate(&C.ev0)) != cudaSuccess || (e = cudaEventCreate(&C.ev1)) != cudaSuccess) {
+      st = fail(C, PNS_ERR_CUDA, "event", e);
+      break;
+    }
+  } while (0);
+  if (st != PNS_OK) {
+    delete ctx;
+    return st;
+  }
+  C.t_setup_ms = now_ms() - t0;
+  *out = ctx;
+  return PNS_OK;
+}
+
+void pns_destroy(pns_ctx* ctx) {
+  if (!ctx) return;
+  if (ctx->c.ev0) cudaEventDestroy(ctx->c.ev0);
+  if (ctx->c.ev1) cudaEventDestroy(ctx->c.ev1);
+  delete ctx;
+}
+
+const char* pns_last_error(const pns_ctx* ctx) { return ctx ? ctx->c.err.c_str() : "null context"; }
+
+int pns_get_info(const pns_ctx* ctx, pns_info* info) {
+  if (check_ctx(ctx) || !info) return PNS_ERR_ARG;
+  const Ctx& C = ctx->c;
+  memset(info, 0, sizeof *info);
+  info->nx = C.G.nx;
+  info->ny = C.G.ny;
+  info->nz = C.G.nz;
+  info->dim = C.G.dim;
+  info->ncell = C.G.ncell;
+  info->n_unknowns = C.M.n_unknowns;
+  info->n_faces = C.M.n_faces;
+  info->n_cells = C.M.n_cells;
+  info->n_prim = C.M.n_prim;
+  info->n_iface = C.M.n_iface;
+  info->n_pins = (int)C.M.pins.size();
+  info->n_dropped_labels = C.M.n_dropped;
+  for (auto& v : C.M.prim_unk) {
+    info->prim_unknowns_total += (long long)v.size();
+    info->prim_sum_n2 += (double)v.size() * v.size();
+    info->max_block = std::max(info->max_block, (int)v.size());
+  }
+  for (auto& v : C.M.dual_unk) {
+    info->dual_unknowns_total += (long long)v.size();
+    info->dual_sum_n2 += (double)v.size() * v.size();
+    info->max_block = std::max(info->max_block, (int)v.size());
+  }
+  size_t bytes = 0;
+  const DevBuf* bufs[] = {&C.flags, &C.owner, &C.cell_iface, &C.pc.prim.mat, &C.pc.dual.mat, &C.pc.basis,
+                          &C.pc.ao_inv, &C.V, &C.Z, &C.w0, &C.w1, &C.w2, &C.w3, &C.w4, &C.pk_x, &C.pk_y};
+  for (auto* p : bufs) bytes += p->bytes;
+  info->device_bytes = bytes;
+  return PNS_OK;
+}
+
+int pns_residual(pns_ctx* ctx, const double* x, const double* x_prev, double* r) {
+  if (check_ctx(ctx) || !x || !r) return PNS_ERR_ARG;
+  Ctx& C = ctx->c;
+  CK(launch_residual(C, 0, x, x_prev, r));
+  return PNS_OK;
+}
+
+int pns_jacobian_apply(pns_ctx* ctx, const double* x_lin, const double* v, double* y) {
+  if (check_ctx(ctx) || !x_lin || !v || !y) return PNS_ERR_ARG;
+  Ctx& C = ctx->c;
+  CK(launch_apply<double>(C, OP_NEWTON, x_lin, v, nullptr, y, true));
+  return PNS_OK;
+}
+
+int pns_operator_apply(pns_ctx* ctx, int variant, const double* x_lin, const double* v, double* y) {
+  if (check_ctx(ctx) || !x_lin || !v || !y || variant < 0 || variant > 3) return PNS_ERR_ARG;
+  Ctx& C = ctx->c;
+  CK(launch_apply<double>(C, op_of_variant(variant), x_lin, v, nullptr, y, true));
+  return PNS_OK;
+}
+
+int pns_build_precond(pns_ctx* ctx, const double* x_lin) {
+  if (check_ctx(ctx) || !x_lin) return PNS_ERR_ARG;
+  Ctx& C = ctx->c;
+  return build_precond(C, C.pc, C.opt.variant, x_lin);
+}
+
+int pns_precond_apply(pns_ctx* ctx, const double* v, double* z) {
+  if (check_ctx(ctx) || !v || !z) return PNS_ERR_ARG;
+  Ctx& C = ctx->c;
+  return precond_apply(C, C.pc, v, z);
+}
+
+int pns_newton_solve(pns_ctx* ctx, double* x, const double* x_prev, pns_stats* st) {
+  if (check_ctx(ctx) || !x) return PNS_ERR_ARG;
+  Ctx& C = ctx->c;
+  if (!C.pc.built) CKS(build_precond(C, C.pc, C.opt.variant, x));
+  return newton(C, C.pc, 0, x, x_prev, st);
+}
+
+int pns_stokes_solve(pns_ctx* ctx, double* x, pns_stats* st) {
+  if (check_ctx(ctx) || !x) return PNS_ERR_ARG;
+  Ctx& C = ctx->c;
+  Precond tmp;
+  CKS(build_precond(C, tmp, PNS_APLMM_S, nullptr));
+  CK(cudaMemsetAsync(x, 0, sizeof(double) * C.nfull, C.stream));
+  int maxn = C.opt.max_newton;
+  C.opt.max_newton = std::min(maxn, 3);
+  int code = newton(C, tmp, 1, x, nullptr, st);
+  C.opt.max_newton = maxn;
+  return code;
+}
+
+int pns_export_maps(const pns_ctx* ctx, int32_t* cell_prim, int32_t* cell_iface, int32_t* face_class, uint8_t* tags,
+                    int32_t* dual_count, int32_t* pins) {
+  if (check_ctx(ctx)) return PNS_ERR_ARG;
+  const Ctx& C = ctx->c;
+  const int nc = C.G.ncell, dim = C.G.dim;
+  if (cell_prim) std::copy(C.M.cell_prim.begin(), C.M.cell_prim.end(), cell_prim);
+  if (cell_iface) std::copy(C.M.cell_iface.begin(), C.M.cell_iface.end(), cell_iface);
+  if (face_class) std::copy(C.M.face_class.begin(), C.M.face_class.end(), face_class);
+  if (tags)
+    for (int d = 0; d < dim; ++d)
+      for (int c = 0; c < nc; ++c) tags[(size_t)d * nc + c] = (C.M.flags[c] & fl_tag(d)) ? 1 : 0;
+  if (dual_count) {
+    std::fill(dual_count, dual_count + (size_t)(dim + 1) * nc, 0);
+    for (auto& v : C.M.dual_unk)
+      for (int g : v) dual_count[g]++;
+  }
+  if (pins) std::copy(C.M.pins.begin(), C.M.pins.end(), pins);
+  return PNS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,237 @@
+"""Python binding of libpns (include/pns.h): ctypes marshalling only.  Every step of the solver runs
+inside the CUDA library; this module converts tensors to device pointers and status codes to
+exceptions.  It refuses to run without the compiled library or without a CUDA device."""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libpns.so")
+
+GPLMM, APLMM_NS, APLMM_S, ML_ONLY = 0, 1, 2, 3
+VARIANTS = {"gplmm": GPLMM, "aplmm_ns": APLMM_NS, "aplmm_s": APLMM_S, "ml_only": ML_ONLY}
+FP64, FP32, BF16 = 0, 1, 2
+PRECISIONS = {"fp64": FP64, "fp32": FP32, "bf16": BF16}
+COMBINE_BUILD, COMBINE_CURRENT = 0, 1
+
+STATUS = {0: "PNS_OK", -1: "PNS_ERR_ARG", -2: "PNS_ERR_CUDA", -3: "PNS_ERR_OOM", -4: "PNS_ERR_SINGULAR",
+          -5: "PNS_ERR_NOT_CONVERGED", -6: "PNS_ERR_NAN", -7: "PNS_ERR_STATE", -8: "PNS_ERR_TIMEOUT"}
+
+
+class PnsError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("periodic", ctypes.c_int * 3), ("variant", ctypes.c_int), ("precision", ctypes.c_int),
+                ("combine", ctypes.c_int), ("n_dilate", ctypes.c_int), ("n_tag", ctypes.c_int),
+                ("restart", ctypes.c_int), ("max_fgmres", ctypes.c_int), ("max_newton", ctypes.c_int),
+                ("inner_tol", ctypes.c_double), ("newton_tol", ctypes.c_double), ("refine_steps", ctypes.c_int),
+                ("timing", ctypes.c_int), ("stream", ctypes.c_void_p)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("newton_its", ctypes.c_int), ("fgmres_its_total", ctypes.c_int),
+                ("fgmres_its", ctypes.c_int * 64), ("res_hist", ctypes.c_double * 65),
+                ("r0_norm", ctypes.c_double), ("t_setup_ms", ctypes.c_double), ("t_mg_ms", ctypes.c_double),
+                ("t_ml_ms", ctypes.c_double), ("t_sol_ms", ctypes.c_double), ("t_local_ms", ctypes.c_double),
+                ("local_launches", ctypes.c_longlong), ("local_bytes_per_apply", ctypes.c_double)]
+
+    def as_dict(self):
+        n = self.newton_its
+        return {"newton_its": n, "fgmres_its_total": self.fgmres_its_total,
+                "fgmres_its": list(self.fgmres_its[:min(n, 64)]), "res_hist": list(self.res_hist[:min(n + 1, 65)]),
+                "r0_norm": self.r0_norm, "t_setup_ms": self.t_setup_ms, "t_mg_ms": self.t_mg_ms,
+                "t_ml_ms": self.t_ml_ms, "t_sol_ms": self.t_sol_ms, "t_local_ms": self.t_local_ms,
+                "local_launches": self.local_launches, "local_bytes_per_apply": self.local_bytes_per_apply}
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int), ("dim", ctypes.c_int),
+                ("ncell", ctypes.c_longlong), ("n_unknowns", ctypes.c_longlong), ("n_faces", ctypes.c_longlong),
+                ("n_cells", ctypes.c_longlong), ("n_prim", ctypes.c_int), ("n_iface", ctypes.c_int),
+                ("n_pins", ctypes.c_int), ("n_dropped_labels", ctypes.c_int),
+                ("prim_unknowns_total", ctypes.c_longlong), ("dual_unknowns_total", ctypes.c_longlong),
+                ("prim_sum_n2", ctypes.c_double), ("dual_sum_n2", ctypes.c_double), ("max_block", ctypes.c_int),
+                ("device_bytes", ctypes.c_size_t)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libpns.so (built by __graft_entry__.build()).  Raises when it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libpns.so not built ({path}); run __graft_entry__.build()")
+    lib = ctypes.CDLL(path)
+    P, I, D, V = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, None
+    sig = {
+        "pns_default_options": (V, [ctypes.POINTER(Options)]),
+        "pns_setup": (I, [ctypes.POINTER(P), I, I, I, P, P, D, D, ctypes.POINTER(D), D, ctypes.POINTER(Options)]),
+        "pns_destroy": (V, [P]),
+        "pns_last_error": (ctypes.c_char_p, [P]),
+        "pns_get_info": (I, [P, ctypes.POINTER(Info)]),
+        "pns_residual": (I, [P, P, P, P]),
+        "pns_jacobian_apply": (I, [P, P, P, P]),
+        "pns_operator_apply": (I, [P, I, P, P, P]),
+        "pns_build_precond": (I, [P, P]),
+        "pns_precond_apply": (I, [P, P, P]),
+        "pns_newton_solve": (I, [P, P, P, ctypes.POINTER(Stats)]),
+        "pns_stokes_solve": (I, [P, P, ctypes.POINTER(Stats)]),
+        "pns_export_maps": (I, [P, P, P, P, P, P, P]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def default_options() -> Options:
+    o = Options()
+    load().pns_default_options(ctypes.byref(o))
+    return o
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise TypeError("expected a contiguous float64 CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Solver:
+    """One pns context: geometry, parameters, maps and (once built) a preconditioner."""
+
+    def __init__(self, mask, labels, rho, mu, b, dt=0.0, variant="gplmm", precision="fp64", combine="build",
+                 periodic=(True, False, False), n_dilate=1, n_tag=1, restart=100, max_fgmres=2000, max_newton=30,
+                 inner_tol=1e-9, newton_tol=1e-8, timing=False, stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("libpns needs a CUDA device")
+        self.lib = load()
+        mask = np.ascontiguousarray(mask, dtype=np.uint8)
+        labels = np.ascontiguousarray(labels, dtype=np.int32)
+        if mask.ndim != 3 or labels.shape != mask.shape:
+            raise ValueError("mask and labels must be (nz, ny, nx) arrays of equal shape")
+        self.shape = mask.shape
+        nz, ny, nx = mask.shape
+        self.dim = 2 if nz == 1 else 3
+        self.ncell = nx * ny * nz
+        self.nfull = (self.dim + 1) * self.ncell
+        o = default_options()
+        o.periodic[:] = [int(p) for p in periodic]
+        o.variant = VARIANTS[variant] if isinstance(variant, str) else int(variant)
+        o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        o.combine = COMBINE_BUILD if combine == "build" else COMBINE_CURRENT
+        o.n_dilate, o.n_tag, o.restart = n_dilate, n_tag, restart
+        o.max_fgmres, o.max_newton = max_fgmres, max_newton
+        o.inner_tol, o.newton_tol = inner_tol, newton_tol
+        o.timing = int(bool(timing))
+        s = stream if stream is not None else torch.cuda.current_stream()
+        o.stream = ctypes.c_void_p(s.cuda_stream)
+        self.stream = s
+        self.options = o
+        bb = (ctypes.c_double * 3)(*(list(b) + [0.0] * (3 - len(b))))
+        ctx = ctypes.c_void_p()
+        rc = self.lib.pns_setup(ctypes.byref(ctx), nz, ny, nx, mask.ctypes.data_as(ctypes.c_void_p),
+                                labels.ctypes.data_as(ctypes.c_void_p), float(rho), float(mu), bb, float(dt),
+                                ctypes.byref(o))
+        if rc != 0:
+            raise PnsError(rc, "pns_setup failed (bad mask/labels/parameters or CUDA error)")
+        self.ctx = ctx
+
+    def __del__(self):
+        ctx = getattr(self, "ctx", None)
+        if ctx:
+            self.lib.pns_destroy(ctx)
+            self.ctx = None
+
+    def close(self):
+        self.__del__()
+
+    def _check(self, rc, what):
+        if rc != 0:
+            raise PnsError(rc, f"{what}: {self.lib.pns_last_error(self.ctx).decode()}")
+
+    def zeros(self):
+        import torch
+        return torch.zeros(self.nfull, dtype=torch.float64, device="cuda")
+
+    # --- C-ABI calls (same names as include/pns.h)
+    def info(self):
+        inf = Info()
+        self._check(self.lib.pns_get_info(self.ctx, ctypes.byref(inf)), "pns_get_info")
+        return inf.as_dict()
+
+    def pns_residual(self, x, x_prev=None, r=None):
+        r = self.zeros() if r is None else r
+        self._check(self.lib.pns_residual(self.ctx, _ptr(x), _ptr(x_prev), _ptr(r)), "pns_residual")
+        return r
+
+    def pns_jacobian_apply(self, x_lin, v, y=None):
+        y = self.zeros() if y is None else y
+        self._check(self.lib.pns_jacobian_apply(self.ctx, _ptr(x_lin), _ptr(v), _ptr(y)), "pns_jacobian_apply")
+        return y
+
+    def pns_operator_apply(self, variant, x_lin, v, y=None):
+        y = self.zeros() if y is None else y
+        var = VARIANTS[variant] if isinstance(variant, str) else int(variant)
+        self._check(self.lib.pns_operator_apply(self.ctx, var, _ptr(x_lin), _ptr(v), _ptr(y)), "pns_operator_apply")
+        return y
+
+    def pns_build_precond(self, x_lin):
+        self._check(self.lib.pns_build_precond(self.ctx, _ptr(x_lin)), "pns_build_precond")
+
+    def pns_precond_apply(self, v, z=None):
+        z = self.zeros() if z is None else z
+        self._check(self.lib.pns_precond_apply(self.ctx, _ptr(v), _ptr(z)), "pns_precond_apply")
+        return z
+
+    def pns_newton_solve(self, x, x_prev=None, check=True):
+        st = Stats()
+        rc = self.lib.pns_newton_solve(self.ctx, _ptr(x), _ptr(x_prev), ctypes.byref(st))
+        if check:
+            self._check(rc, "pns_newton_solve")
+        d = st.as_dict()
+        d["status"] = STATUS.get(rc, rc)
+        return d
+
+    def pns_stokes_solve(self, x=None, check=True):
+        x = self.zeros() if x is None else x
+        st = Stats()
+        rc = self.lib.pns_stokes_solve(self.ctx, _ptr(x), ctypes.byref(st))
+        if check:
+            self._check(rc, "pns_stokes_solve")
+        d = st.as_dict()
+        d["status"] = STATUS.get(rc, rc)
+        return x, d
+
+    def pns_export_maps(self):
+        nc, dim = self.ncell, self.dim
+        cell_prim = np.zeros(nc, np.int32)
+        cell_iface = np.zeros(nc, np.int32)
+        face_class = np.zeros(dim * nc, np.int32)
+        tags = np.zeros(dim * nc, np.uint8)
+        dual_count = np.zeros((dim + 1) * nc, np.int32)
+        n_pins = self.info()["n_pins"]
+        pins = np.zeros(max(1, n_pins), np.int32)
+        P = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+        self._check(self.lib.pns_export_maps(self.ctx, P(cell_prim), P(cell_iface), P(face_class), P(tags),
+                                             P(dual_count), P(pins)), "pns_export_maps")
+        return {"cell_prim": cell_prim, "cell_iface": cell_iface, "face_class": face_class.reshape(dim, nc),
+                "tags": tags.reshape(dim, nc).astype(bool), "dual_count": dual_count, "pins": pins[:n_pins]}

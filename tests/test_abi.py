@@ -1,0 +1,52 @@
+"""The C-ABI library loads and exports every entry point that include/pns.h declares (no GPU and
+no compute calls needed)."""
+import os
+import re
+import shutil
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "pns.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(pns_[a-z_]+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for n in ["pns_setup", "pns_residual", "pns_jacobian_apply", "pns_precond_apply", "pns_newton_solve",
+              "pns_build_precond", "pns_stokes_solve", "pns_export_maps", "pns_destroy", "pns_last_error"]:
+        assert n in names
+
+
+@pytest.fixture(scope="module")
+def lib_path():
+    from paper_2510_22077_gb300 import build, pns
+    if not os.path.exists(pns.LIB_PATH):
+        if shutil.which("nvcc") is None and not os.path.exists("/usr/local/cuda/bin/nvcc"):
+            pytest.skip("nvcc not available to build libpns")
+        build.build()
+    return pns.LIB_PATH
+
+
+def test_library_exports_every_declared_symbol(lib_path):
+    out = subprocess.run(["nm", "-D", "--defined-only", lib_path], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\bT (pns_[a-z_]+)$", out, flags=re.M))
+    missing = [n for n in _declared() if n not in exported]
+    assert not missing, missing
+
+
+def test_library_loads_with_ctypes(lib_path):
+    import ctypes
+    lib = ctypes.CDLL(lib_path)
+    for n in _declared():
+        assert hasattr(lib, n)
+    # pure host call: default options
+    from paper_2510_22077_gb300 import pns
+    pns._lib = None
+    o = pns.default_options()
+    assert o.restart == 100 and o.periodic[0] == 1 and abs(o.newton_tol - 1e-8) < 1e-20
