@@ -86,7 +86,7 @@ typedef struct pns_options {
   double inner_tol;      /* FGMRES: stop when ||J d + r|| < inner_tol * ||r(0)|| (default 1e-9) */
   double newton_tol;     /* Newton: stop when ||r(x)|| < newton_tol * ||r(0)|| (default 1e-8) */
   int refine_steps;      /* Newton-Schulz steps X <- X + X (I - A X) (FP64 residual) applied to the
-                            FP32 local inverses, each block refined while its residual keeps falling fast;
+                            FP32 local inverses whose max |I - A X| exceeds 1e-5, each refined while its residual keeps falling fast;
                             -1 = automatic (up to 3 for FP32/BF16; FP64 inverts in FP64) */
   int timing;            /* 1: record CUDA events around the local-solve kernels (pns_stats) */
   void* stream;          /* cudaStream_t to enqueue on (NULL = legacy default stream) */
@@ -105,6 +105,8 @@ typedef struct pns_stats {
   double t_local_ms;              /* time inside the batched local-solve kernels (timing == 1) */
   long long local_launches;       /* number of batched local-solve launches timed */
   double local_bytes_per_apply;   /* algorithmic bytes of one M_d + M_p local-solve pass */
+  long long kernel_launches;      /* library-wide count of kernel launches so far (all contexts) */
+  double refine_residual_max;     /* max |I - A X| of the FP32 local inverses before refinement */
 } pns_stats;
 
 typedef struct pns_info {
@@ -169,6 +171,12 @@ int pns_newton_solve(pns_ctx* ctx, double* x, const double* x_prev, pns_stats* s
  * nearby wind exists.  Builds an aPLMM_S preconditioner internally (kept separately from the one
  * of pns_build_precond) and runs FGMRES on the linear system.  x: device, output.  Synchronises. */
 int pns_stokes_solve(pns_ctx* ctx, double* x, pns_stats* st);
+
+/* Copy the inverse of the coarse matrix A^o = R^ A_b P^ (Remark 1) of the built preconditioner to a
+ * HOST array of n_o * n_o doubles (row-major); *n_o receives the coarse size (coarse interfaces
+ * first, then primary grids).  ao_inv may be NULL to query n_o.  PNS_ERR_STATE before a build or
+ * for ML_ONLY.  Synchronises. */
+int pns_export_coarse(const pns_ctx* ctx, double* ao_inv, int* n_o);
 
 /* Copy the integer maps to HOST arrays (for bit-exact tests).  Any pointer may be NULL.
  *   cell_prim[ncell]   primary grid of each cell (-1: interface cell or solid)

@@ -98,14 +98,20 @@ struct Ctx {
   int m_alloc = 0;
   DevBuf V, Z, H, givens, hvec, partial;
   DevBuf xk, rk, dx;
-  // timing
+  // timing: event pairs around the batched local solves, read after the solve synchronises
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
   double t_local_ms = 0;
   long long local_launches = 0;
   const double* cur_state = nullptr;   // Newton state for COMBINE_CURRENT
   double t_setup_ms = 0;
   double t_mg_ms = 0, t_ml_ms = 0;
 };
+
+// Counts every kernel launch of the library (all contexts); read through pns_stats.
+void count_launch();
+long long launch_count();
 
 // ---------------------------------------------------------------- launchers (kernels_*.cu)
 // stencil
@@ -136,6 +142,22 @@ cudaError_t launch_closure_residual(const Ctx& C, const BlockSet& B, int op, con
                                     const long long* d_roff, const int* d_kc, const double* rhs, const double* S,
                                     double* res);
 cudaError_t launch_add_vec(double* a, const double* b, long long n, cudaStream_t s);
+
+// Closure-block solves by the Woodbury identity on the primary-block inverses (see kernels_dense.cu)
+struct WoodburyImpl;
+struct Woodbury {
+  WoodburyImpl* impl;
+  Woodbury();
+  ~Woodbury();
+  Woodbury(const Woodbury&) = delete;
+  Woodbury& operator=(const Woodbury&) = delete;
+  template <typename ST>
+  cudaError_t setup(const Ctx& C, const BlockSet& B, int op, const double* state, const ST* X,
+                    const std::vector<int>& kc, int* d_bad);
+  template <typename ST>
+  cudaError_t apply(const Ctx& C, const BlockSet& B, const ST* X, const double* R, double* S, double* Y,
+                    const long long* d_roff, const int* d_kc, const std::vector<int>& kc);
+};
 
 // coarse
 cudaError_t launch_seg_sum(const Precond& pc, const void* v, int vt_is_double, double* out, cudaStream_t s);

@@ -117,6 +117,7 @@ __global__ void k_cpiv(double* __restrict__ A, int n, int t, double* __restrict_
     pv = 1.0;
   }
   if (threadIdx.x == 0) perm[t] = p;
+  __syncthreads();   // every thread has read the pivot value before any thread swaps rows t and p
   if (p != t)
     for (int j = threadIdx.x; j < n; j += blockDim.x) {
       double a = A[(long long)t * n + j];
@@ -173,11 +174,11 @@ cudaError_t launch_seg_sum(const Precond& pc, const void* v, int vt_is_double, d
   cudaMemsetAsync(out, 0, sizeof(double) * pc.n_o, s);
   if (pc.nseg_items == 0) return cudaGetLastError();
   if (vt_is_double)
-    k_seg_sum<double><<<pc.nseg_items, 256, 0, s>>>(pc.seg_items.as<int2>(), pc.seg_idx.as<int>(),
-                                                    pc.seg_off.as<long long>(), (const double*)v, out);
+    { pns::count_launch(); k_seg_sum<double><<<pc.nseg_items, 256, 0, s>>>(pc.seg_items.as<int2>(), pc.seg_idx.as<int>(),
+                                                    pc.seg_off.as<long long>(), (const double*)v, out); }
   else
-    k_seg_sum<float><<<pc.nseg_items, 256, 0, s>>>(pc.seg_items.as<int2>(), pc.seg_idx.as<int>(),
-                                                   pc.seg_off.as<long long>(), (const float*)v, out);
+    { pns::count_launch(); k_seg_sum<float><<<pc.nseg_items, 256, 0, s>>>(pc.seg_items.as<int2>(), pc.seg_idx.as<int>(),
+                                                   pc.seg_off.as<long long>(), (const float*)v, out); }
   return cudaGetLastError();
 }
 
@@ -187,16 +188,16 @@ cudaError_t launch_prolong(const Ctx& C, const Precond& pc, const double* xo, VT
   const BlockSet& B = pc.prim;
   if (B.nblk > 0) {
     long long blk = (B.n_total + 255) / 256;
-    k_prolong_prim<ST, VT><<<(unsigned)blk, 256, 0, C.stream>>>(
+    { pns::count_launch(); k_prolong_prim<ST, VT><<<(unsigned)blk, 256, 0, C.stream>>>(
         B.nblk, B.d_ioff.as<long long>(), B.d_n.as<int>(), B.idx.as<int>(), B.n_total, pc.basis.as<ST>(),
-        pc.d_boff.as<long long>(), pc.d_kcols.as<int>(), pc.d_colid.as<int>(), pc.d_coloff.as<int>(), xo, z);
+        pc.d_boff.as<long long>(), pc.d_kcols.as<int>(), pc.d_colid.as<int>(), pc.d_coloff.as<int>(), xo, z); }
   }
   int nif = pc.n_cif;
   if (nif > 0) {
     long long tot = 0;
     for (int j : C.M.coarse_ifaces) tot += (long long)C.M.iface_cells[j].size();
     long long blk = (tot + 255) / 256;
-    k_prolong_iface<VT><<<(unsigned)blk, 256, 0, C.stream>>>(pc.seg_idx.as<int>(), pc.seg_off.as<long long>(), nif, xo, z);
+    { pns::count_launch(); k_prolong_iface<VT><<<(unsigned)blk, 256, 0, C.stream>>>(pc.seg_idx.as<int>(), pc.seg_off.as<long long>(), nif, xo, z); }
   }
   return cudaGetLastError();
 }
@@ -208,10 +209,10 @@ cudaError_t launch_coarse_invert(double* A, int n, double* work, int* perm, int*
   long long nn = (long long)n * n;
   unsigned blk = (unsigned)((nn + 255) / 256);
   for (int t = 0; t < n; ++t) {
-    k_cpiv<<<1, 1024, 0, s>>>(A, n, t, work, perm, d_bad);
-    k_celim<<<blk, 256, 0, s>>>(A, n, t, work);
+    { pns::count_launch(); k_cpiv<<<1, 1024, 0, s>>>(A, n, t, work, perm, d_bad); }
+    { pns::count_launch(); k_celim<<<blk, 256, 0, s>>>(A, n, t, work); }
   }
-  k_cunperm<<<(n + 127) / 128, 128, 0, s>>>(A, n, perm);
+  { pns::count_launch(); k_cunperm<<<(n + 127) / 128, 128, 0, s>>>(A, n, perm); }
   return cudaGetLastError();
 }
 
@@ -219,7 +220,7 @@ template <typename ST>
 cudaError_t launch_coarse_gemv(const ST* Ainv, int n, const double* rhs, double* x, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
   long long thr = (long long)n * 32;
-  k_cgemv<ST><<<(unsigned)((thr + 255) / 256), 256, 0, s>>>(Ainv, n, rhs, x);
+  { pns::count_launch(); k_cgemv<ST><<<(unsigned)((thr + 255) / 256), 256, 0, s>>>(Ainv, n, rhs, x); }
   return cudaGetLastError();
 }
 template cudaError_t launch_coarse_gemv<double>(const double*, int, const double*, double*, cudaStream_t);

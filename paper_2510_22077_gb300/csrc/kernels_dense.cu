@@ -567,6 +567,222 @@ __global__ void k_add_vec(double* __restrict__ a, const double* __restrict__ b, 
     a[i] += b[i];
 }
 
+// ------------------------------------------------------------------------------ Woodbury closure
+// The closure block Abar = A_p + E_K diag(delta) E_K^T differs from the primary block A_p only on the
+// diagonal entries K of rows coupled to interface faces or other primary grids (Eqs. 6, 9), so
+// Abar^{-1} R = X R - X_{:,K} (diag(delta)^{-1} + X_KK)^{-1} (X R)_K with X = A_p^{-1} already built.
+
+// extra[t] = sum of A_b couplings of primary row t to f faces and other primary grids
+__global__ void k_closure_extras(Geo G, Phy P, const uint8_t* __restrict__ fl, int op, const double* __restrict__ st,
+                                 const int* __restrict__ owner, int nblk, const long long* __restrict__ ioff,
+                                 const int* __restrict__ bn, const int* __restrict__ idx, long long n_total,
+                                 double* __restrict__ extra) {
+  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= n_total) return;
+  int b = find_block(ioff, nblk, t);
+  int r = (int)(t - ioff[b]);
+  if (r >= bn[b]) { extra[t] = 0.0; return; }
+  int g = idx[t];
+  RowList L;
+  L.n = 0;
+  any_row<double>(G, P, fl, op, st, g, L);
+  int me = owner[g];
+  double e = 0.0;
+  for (int k = 0; k < L.n; ++k) {
+    int o = owner[L.col[k]];
+    if (o == -3 || (o >= 0 && o != me)) e += L.val[k];
+  }
+  extra[t] = e;
+}
+
+// Cap_b[i][j] = X_b[K_i][K_j] + (i == j) / delta_i   (FP64, row-major k x k)
+template <typename ST>
+__global__ void k_cap_assemble(const int* __restrict__ order_blk, const long long* __restrict__ epre, int nb,
+                               const int* __restrict__ kv, const long long* __restrict__ koff,
+                               const long long* __restrict__ cmoff, const int* __restrict__ Klist,
+                               const double* __restrict__ delta, const int* __restrict__ bld,
+                               const long long* __restrict__ moff, const ST* __restrict__ X, double* __restrict__ cap) {
+  long long w = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (w >= epre[nb]) return;
+  int s = find_block(epre, nb, w);
+  int b = order_blk[s];
+  long long loc = w - epre[s];
+  int k = kv[b];
+  int i = (int)(loc / k), j = (int)(loc % k);
+  const int* K = Klist + koff[b];
+  double v = (double)X[moff[b] + (long long)K[i] * bld[b] + K[j]];
+  if (i == j) v += 1.0 / delta[koff[b] + i];
+  cap[cmoff[b] + loc] = v;
+}
+
+// batched Gauss-Jordan with partial pivoting on the active blocks (order[0 .. cnt) all have k > t)
+__global__ void k_bpiv(int t, const int* __restrict__ order, const int* __restrict__ kv,
+                       const long long* __restrict__ cmoff, const long long* __restrict__ koff, double* __restrict__ cap,
+                       double* __restrict__ colw, int* __restrict__ perm, int* __restrict__ bad) {
+  __shared__ double bv[256];
+  __shared__ int bi[256];
+  int b = order[blockIdx.x];
+  int k = kv[b];
+  double* A = cap + cmoff[b];
+  double best = -1.0;
+  int arg = t;
+  for (int i = t + threadIdx.x; i < k; i += blockDim.x) {
+    double v = fabs(A[(long long)i * k + t]);
+    if (v > best) { best = v; arg = i; }
+  }
+  bv[threadIdx.x] = best;
+  bi[threadIdx.x] = arg;
+  __syncthreads();
+  for (int sft = blockDim.x / 2; sft > 0; sft >>= 1) {
+    if (threadIdx.x < sft) {
+      if (bv[threadIdx.x + sft] > bv[threadIdx.x] ||
+          (bv[threadIdx.x + sft] == bv[threadIdx.x] && bi[threadIdx.x + sft] < bi[threadIdx.x])) {
+        bv[threadIdx.x] = bv[threadIdx.x + sft];
+        bi[threadIdx.x] = bi[threadIdx.x + sft];
+      }
+    }
+    __syncthreads();
+  }
+  int p = bi[0];
+  double pv = A[(long long)p * k + t];
+  if (!(bv[0] > 0.0) || !(bv[0] < 1e300)) {
+    if (threadIdx.x == 0) atomicExch(bad, 1);
+    pv = 1.0;
+  }
+  if (threadIdx.x == 0) perm[koff[b] + t] = p;
+  __syncthreads();   // every thread has read the pivot value before any thread swaps rows t and p
+  if (p != t)
+    for (int j = threadIdx.x; j < k; j += blockDim.x) {
+      double a = A[(long long)t * k + j];
+      A[(long long)t * k + j] = A[(long long)p * k + j];
+      A[(long long)p * k + j] = a;
+    }
+  __syncthreads();
+  double* col = colw + koff[b];
+  for (int i = threadIdx.x; i < k; i += blockDim.x) col[i] = A[(long long)i * k + t];
+  __syncthreads();
+  double inv = 1.0 / pv;
+  for (int j = threadIdx.x; j < k; j += blockDim.x) A[(long long)t * k + j] = (j == t) ? inv : A[(long long)t * k + j] * inv;
+}
+
+__global__ void k_belim(int t, const int* __restrict__ order, const long long* __restrict__ epre, int cnt,
+                        const int* __restrict__ kv, const long long* __restrict__ cmoff,
+                        const long long* __restrict__ koff, double* __restrict__ cap, const double* __restrict__ colw) {
+  long long w = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (w >= epre[cnt]) return;
+  int s = find_block(epre, cnt, w);
+  int b = order[s];
+  long long loc = w - epre[s];
+  int k = kv[b];
+  int i = (int)(loc / k), j = (int)(loc % k);
+  if (i == t) return;
+  double* A = cap + cmoff[b];
+  double f = colw[koff[b] + i];
+  if (j == t) A[loc] = -f * A[(long long)t * k + t];
+  else A[loc] -= f * A[(long long)t * k + j];
+}
+
+__global__ void k_bunperm(int nb, const long long* __restrict__ rpre, const int* __restrict__ kv,
+                          const long long* __restrict__ cmoff, const long long* __restrict__ koff,
+                          double* __restrict__ cap, const int* __restrict__ perm) {
+  long long w = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (w >= rpre[nb]) return;
+  int b = find_block(rpre, nb, w);
+  int i = (int)(w - rpre[b]);
+  int k = kv[b];
+  double* row = cap + cmoff[b] + (long long)i * k;
+  const int* pr = perm + koff[b];
+  for (int t = k - 1; t >= 0; --t) {
+    int p = pr[t];
+    if (p != t) {
+      double a = row[t];
+      row[t] = row[p];
+      row[p] = a;
+    }
+  }
+}
+
+// W[b] (k x kc) = Y[b][K, :]
+__global__ void k_gather_rows(int nb, const long long* __restrict__ rpre, const int* __restrict__ kv,
+                              const long long* __restrict__ koff, const int* __restrict__ Klist,
+                              const long long* __restrict__ roff, const long long* __restrict__ woff,
+                              const int* __restrict__ kcv, const double* __restrict__ Y, double* __restrict__ W) {
+  long long w = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (w >= rpre[nb]) return;
+  int b = find_block(rpre, nb, w);
+  int m = (int)(w - rpre[b]);
+  int kc = kcv[b];
+  int r = Klist[koff[b] + m];
+  for (int q = 0; q < kc; ++q) W[woff[b] + (long long)m * kc + q] = Y[roff[b] + (long long)r * kc + q];
+}
+
+// Z[b] (k x kc) = Cinv[b] (k x k) * W[b]   (warp per row)
+__global__ void k_cap_mm(int nb, const long long* __restrict__ rpre, const int* __restrict__ kv,
+                         const long long* __restrict__ cmoff, const double* __restrict__ Cinv,
+                         const long long* __restrict__ woff, const int* __restrict__ kcv, const double* __restrict__ W,
+                         double* __restrict__ Z) {
+  long long w = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (w >= rpre[nb]) return;
+  int b = find_block(rpre, nb, w);
+  int m = (int)(w - rpre[b]);
+  int k = kv[b], kc = kcv[b];
+  const double* C = Cinv + cmoff[b] + (long long)m * k;
+  for (int q0 = 0; q0 < kc; q0 += 16) {
+    int qn = min(16, kc - q0);
+    double acc[16];
+    for (int q = 0; q < 16; ++q) acc[q] = 0.0;
+    for (int j = lane; j < k; j += 32) {
+      double c = C[j];
+      const double* wr = W + woff[b] + (long long)j * kc + q0;
+      for (int q = 0; q < qn; ++q) acc[q] += c * wr[q];
+    }
+    for (int q = 0; q < qn; ++q) {
+      double v = acc[q];
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) Z[woff[b] + (long long)m * kc + q0 + q] = v;
+    }
+  }
+}
+
+// S[b][r][:] = Y[b][r][:] - sum_m X_b[r][K_m] Z[b][m][:]   (warp per row of every primary block)
+template <typename ST>
+__global__ void k_woodbury_update(int nblk, const long long* __restrict__ ioff, const int* __restrict__ bn,
+                                  const int* __restrict__ bld, const long long* __restrict__ moff,
+                                  const ST* __restrict__ X, long long n_total, const int* __restrict__ kv,
+                                  const long long* __restrict__ koff, const int* __restrict__ Klist,
+                                  const long long* __restrict__ roff, const long long* __restrict__ woff,
+                                  const int* __restrict__ kcv, const double* __restrict__ Y,
+                                  const double* __restrict__ Z, double* __restrict__ S) {
+  long long t = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (t >= n_total) return;
+  int b = find_block(ioff, nblk, t);
+  int r = (int)(t - ioff[b]);
+  if (r >= bn[b]) return;
+  int k = kv[b], kc = kcv[b];
+  const ST* xr = X + moff[b] + (long long)r * bld[b];
+  const int* K = Klist + koff[b];
+  for (int q0 = 0; q0 < kc; q0 += 16) {
+    int qn = min(16, kc - q0);
+    double acc[16];
+    for (int q = 0; q < 16; ++q) acc[q] = 0.0;
+    for (int m = lane; m < k; m += 32) {
+      double xv = (double)xr[K[m]];
+      const double* zr = Z + woff[b] + (long long)m * kc + q0;
+      for (int q = 0; q < qn; ++q) acc[q] += xv * zr[q];
+    }
+    for (int q = 0; q < qn; ++q) {
+      double v = acc[q];
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) {
+        long long at = roff[b] + (long long)r * kc + q0 + q;
+        S[at] = Y[at] - v;
+      }
+    }
+  }
+}
+
 }  // namespace
 
 // ================================================================================ launchers
@@ -575,10 +791,10 @@ cudaError_t launch_assemble(const Ctx& C, const BlockSet& B, int op, const doubl
   if (B.nblk == 0) return cudaSuccess;
   int thr = 128;
   long long blk = (B.n_total + thr - 1) / thr;
-  k_assemble<ST><<<(unsigned)blk, thr, 0, C.stream>>>(C.G, C.P, C.flags.as<uint8_t>(), op, state, C.owner.as<int>(),
+  { pns::count_launch(); k_assemble<ST><<<(unsigned)blk, thr, 0, C.stream>>>(C.G, C.P, C.flags.as<uint8_t>(), op, state, C.owner.as<int>(),
                                                       B.nblk, B.d_ioff.as<long long>(), B.d_n.as<int>(),
                                                       B.d_ld.as<int>(), B.d_moff.as<long long>(), B.idx.as<int>(),
-                                                      B.n_total, mat, closure);
+                                                      B.n_total, mat, closure); }
   return cudaGetLastError();
 }
 template cudaError_t launch_assemble<double>(const Ctx&, const BlockSet&, int, const double*, double*, int);
@@ -618,16 +834,16 @@ cudaError_t launch_gj_invert(const BlockSet& B, ST* mat, int* d_bad, cudaStream_
   int cnt = B.nblk;
   for (int k = 0; k < Tmax; ++k) {
     while (cnt > 0 && T[order[cnt - 1]] <= k) --cnt;
-    k_gj_diag<ST><<<cnt, 256, 0, s>>>(k, d_order, B.d_n.as<int>(), B.d_ld.as<int>(), B.d_moff.as<long long>(), mat,
-                                      d_bad);
+    { pns::count_launch(); k_gj_diag<ST><<<cnt, 256, 0, s>>>(k, d_order, B.d_n.as<int>(), B.d_ld.as<int>(), B.d_moff.as<long long>(), mat,
+                                      d_bad); }
     if (pre1[cnt] > 0) {
-      k_gj_rowpanel<ST><<<(unsigned)pre1[cnt], 256, smem, s>>>(k, cnt, d_order, d_pre1, B.d_n.as<int>(),
-                                                               B.d_ld.as<int>(), B.d_moff.as<long long>(), mat);
+      { pns::count_launch(); k_gj_rowpanel<ST><<<(unsigned)pre1[cnt], 256, smem, s>>>(k, cnt, d_order, d_pre1, B.d_n.as<int>(),
+                                                               B.d_ld.as<int>(), B.d_moff.as<long long>(), mat); }
       if (pre2[cnt] > 0)
-        k_gj_update<ST><<<(unsigned)pre2[cnt], 256, smem, s>>>(k, cnt, d_order, d_pre2, B.d_n.as<int>(),
-                                                               B.d_ld.as<int>(), B.d_moff.as<long long>(), mat);
-      k_gj_colpanel<ST><<<(unsigned)pre1[cnt], 256, smem, s>>>(k, cnt, d_order, d_pre1, B.d_n.as<int>(),
-                                                               B.d_ld.as<int>(), B.d_moff.as<long long>(), mat);
+        { pns::count_launch(); k_gj_update<ST><<<(unsigned)pre2[cnt], 256, smem, s>>>(k, cnt, d_order, d_pre2, B.d_n.as<int>(),
+                                                               B.d_ld.as<int>(), B.d_moff.as<long long>(), mat); }
+      { pns::count_launch(); k_gj_colpanel<ST><<<(unsigned)pre1[cnt], 256, smem, s>>>(k, cnt, d_order, d_pre1, B.d_n.as<int>(),
+                                                               B.d_ld.as<int>(), B.d_moff.as<long long>(), mat); }
     }
     if ((e = cudaGetLastError()) != cudaSuccess) break;
   }
@@ -646,10 +862,10 @@ cudaError_t launch_closure_rhs(const Ctx& C, const BlockSet& B, int op, const do
   if (B.nblk == 0) return cudaSuccess;
   int thr = 128;
   long long blk = (B.n_total + thr - 1) / thr;
-  k_closure_rhs<<<(unsigned)blk, thr, 0, C.stream>>>(C.G, C.P, C.flags.as<uint8_t>(), op, state,
+  { pns::count_launch(); k_closure_rhs<<<(unsigned)blk, thr, 0, C.stream>>>(C.G, C.P, C.flags.as<uint8_t>(), op, state,
                                                      C.cell_iface.as<int>(), B.nblk, B.d_ioff.as<long long>(),
                                                      B.d_n.as<int>(), B.idx.as<int>(), B.n_total, d_colbase, d_cols,
-                                                     d_roff, d_kc, rhs);
+                                                     d_roff, d_kc, rhs); }
   return cudaGetLastError();
 }
 
@@ -659,9 +875,9 @@ cudaError_t launch_block_mm(const BlockSet& B, const ST* mat, const double* rhs,
   if (B.nblk == 0) return cudaSuccess;
   long long warps = B.n_total;
   long long blk = (warps * 32 + 255) / 256;
-  k_block_mm<ST, AT><<<(unsigned)blk, 256, 0, s>>>(B.nblk, B.d_ioff.as<long long>(), B.d_n.as<int>(),
+  { pns::count_launch(); k_block_mm<ST, AT><<<(unsigned)blk, 256, 0, s>>>(B.nblk, B.d_ioff.as<long long>(), B.d_n.as<int>(),
                                                    B.d_ld.as<int>(), B.d_moff.as<long long>(), mat, B.n_total, rhs,
-                                                   d_roff, d_kc, out);
+                                                   d_roff, d_kc, out); }
   return cudaGetLastError();
 }
 template cudaError_t launch_block_mm<double, double>(const BlockSet&, const double*, const double*, const long long*,
@@ -675,9 +891,9 @@ cudaError_t launch_local_solve(const BlockSet& B, const ST* mat, const double* t
   if (B.nblk == 0) return cudaSuccess;
   int thr = 256;
   long long blk = (B.n_total + thr - 1) / thr;
-  k_gather<PT><<<(unsigned)blk, thr, 0, s>>>(B.idx.as<int>(), B.n_total, t, pk_x);
-  k_local_gemv<ST, PT><<<B.nitems, 256, 0, s>>>(B.items.as<int4>(), B.idx.as<int>(), B.d_ioff.as<long long>(),
-                                                B.d_ld.as<int>(), B.d_moff.as<long long>(), mat, pk_x, z, add);
+  { pns::count_launch(); k_gather<PT><<<(unsigned)blk, thr, 0, s>>>(B.idx.as<int>(), B.n_total, t, pk_x); }
+  { pns::count_launch(); k_local_gemv<ST, PT><<<B.nitems, 256, 0, s>>>(B.items.as<int4>(), B.idx.as<int>(), B.d_ioff.as<long long>(),
+                                                B.d_ld.as<int>(), B.d_moff.as<long long>(), mat, pk_x, z, add); }
   return cudaGetLastError();
 }
 template cudaError_t launch_local_solve<double, double>(const BlockSet&, const double*, const double*, double*,
@@ -730,15 +946,16 @@ cudaError_t launch_ns_refine(const Ctx& C, const BlockSet& B, int op, const doub
       cudaMalloc(&d_rmax, sizeof(unsigned int) * nent);
       if ((e = cudaMalloc(&R, sizeof(AT) * soff[nent])) != cudaSuccess) { cudaFree(d_lst); break; }
       if ((e = cudaMalloc(&T, sizeof(AT) * soff[nent])) != cudaSuccess) { cudaFree(d_lst); cudaFree(R); break; }
+      cudaMemsetAsync(T, 0, sizeof(AT) * soff[nent], s);
       cudaMemcpyAsync(d_lst, lst.data(), sizeof(int) * nent, cudaMemcpyHostToDevice, s);
       cudaMemcpyAsync(d_pre, rowpre.data(), sizeof(long long) * (nent + 1), cudaMemcpyHostToDevice, s);
       cudaMemcpyAsync(d_soff, soff.data(), sizeof(long long) * (nent + 1), cudaMemcpyHostToDevice, s);
       cudaMemsetAsync(d_rmax, 0, sizeof(unsigned int) * nent, s);
       cudaMemsetAsync(R, 0, sizeof(AT) * soff[nent], s);
-      k_ns_residual<ST, AT><<<(unsigned)rowpre[nent], 256, 0, s>>>(
+      { pns::count_launch(); k_ns_residual<ST, AT><<<(unsigned)rowpre[nent], 256, 0, s>>>(
           C.G, C.P, C.flags.as<uint8_t>(), op, state, C.owner.as<int>(), closure, d_lst, d_pre, nent,
           B.d_ioff.as<long long>(), B.d_n.as<int>(), B.d_ld.as<int>(), B.d_moff.as<long long>(), B.idx.as<int>(), mat,
-          d_soff, R, d_rmax);
+          d_soff, R, d_rmax); }
       std::vector<unsigned int> rm(nent);
       cudaMemcpyAsync(rm.data(), d_rmax, sizeof(unsigned int) * nent, cudaMemcpyDeviceToHost, s);
       e = cudaStreamSynchronize(s);
@@ -751,8 +968,7 @@ cudaError_t launch_ns_refine(const Ctx& C, const BlockSet& B, int op, const doub
         if (step == 0) *max_before = std::max(*max_before, (double)v);
         // refine while the residual is above the floor and still falls fast (quadratic phase);
         // once it stalls it sits at the storage-rounding floor cond * eps and further steps are moot
-        // a step from |I - A X| >= 1/2 would not contract (and diverges beyond 1): leave such blocks
-        bool go = v > thresh && v < 0.5f && (step == 0 || v < 0.25 * prev[q]);
+        bool go = v > thresh && (step == 0 || v < 0.25 * prev[q]);
         prev[q] = v;
         if (go) { sel.push_back(lst[q]); ssoff.push_back(soff[q]); }
       }
@@ -775,11 +991,11 @@ cudaError_t launch_ns_refine(const Ctx& C, const BlockSet& B, int op, const doub
         cudaMemcpyAsync(d_tpre, tpre.data(), sizeof(long long) * (ns + 1), cudaMemcpyHostToDevice, s);
         cudaMemcpyAsync(d_epre, epre.data(), sizeof(long long) * (ns + 1), cudaMemcpyHostToDevice, s);
         cudaMemcpyAsync(d_ssoff, ssoff.data(), sizeof(long long) * (ns + 1), cudaMemcpyHostToDevice, s);
-        k_ns_gemm<ST, AT, AT><<<(unsigned)tpre[ns], 256, smem, s>>>(d_sel, d_tpre, ns, B.d_n.as<int>(),
+        { pns::count_launch(); k_ns_gemm<ST, AT, AT><<<(unsigned)tpre[ns], 256, smem, s>>>(d_sel, d_tpre, ns, B.d_n.as<int>(),
                                                                    B.d_ld.as<int>(), B.d_moff.as<long long>(), mat,
-                                                                   d_ssoff, R, T);
-        k_ns_add<ST, AT><<<(unsigned)((epre[ns] + 255) / 256), 256, 0, s>>>(
-            d_sel, d_epre, ns, B.d_n.as<int>(), B.d_ld.as<int>(), B.d_moff.as<long long>(), mat, d_ssoff, T);
+                                                                   d_ssoff, R, T); }
+        { pns::count_launch(); k_ns_add<ST, AT><<<(unsigned)((epre[ns] + 255) / 256), 256, 0, s>>>(
+            d_sel, d_epre, ns, B.d_n.as<int>(), B.d_ld.as<int>(), B.d_moff.as<long long>(), mat, d_ssoff, T); }
         e = cudaStreamSynchronize(s);
         if (e == cudaSuccess) e = cudaGetLastError();
         cudaFree(d_sel);
@@ -824,10 +1040,10 @@ cudaError_t launch_ns_refine(const Ctx& C, const BlockSet& B, int op, const doub
         cudaMemcpyAsync(d_lst, &q, sizeof(int), cudaMemcpyHostToDevice, s);
         cudaMemcpyAsync(d_pre, pre, sizeof pre, cudaMemcpyHostToDevice, s);
         cudaMemsetAsync(d_rmax, 0, sizeof(unsigned int), s);
-        k_ns_residual<ST, AT><<<(unsigned)B.n[q], 256, 0, s>>>(
+        { pns::count_launch(); k_ns_residual<ST, AT><<<(unsigned)B.n[q], 256, 0, s>>>(
             C.G, C.P, C.flags.as<uint8_t>(), op, state, C.owner.as<int>(), closure, d_lst, d_pre, 1,
             B.d_ioff.as<long long>(), B.d_n.as<int>(), B.d_ld.as<int>(), B.d_moff.as<long long>(), B.idx.as<int>(),
-            mat, d_soff, R, d_rmax);
+            mat, d_soff, R, d_rmax); }
         unsigned int rmv = 0;
         cudaMemcpyAsync(&rmv, d_rmax, sizeof rmv, cudaMemcpyDeviceToHost, s);
         e = cudaStreamSynchronize(s);
@@ -855,16 +1071,175 @@ cudaError_t launch_closure_residual(const Ctx& C, const BlockSet& B, int op, con
                                     double* res) {
   if (B.nblk == 0) return cudaSuccess;
   long long blk = (B.n_total + 127) / 128;
-  k_closure_residual<<<(unsigned)blk, 128, 0, C.stream>>>(C.G, C.P, C.flags.as<uint8_t>(), op, state,
+  { pns::count_launch(); k_closure_residual<<<(unsigned)blk, 128, 0, C.stream>>>(C.G, C.P, C.flags.as<uint8_t>(), op, state,
                                                          C.owner.as<int>(), B.nblk, B.d_ioff.as<long long>(),
                                                          B.d_n.as<int>(), B.idx.as<int>(), B.n_total, d_roff, d_kc,
-                                                         rhs, S, res);
+                                                         rhs, S, res); }
   return cudaGetLastError();
 }
 
 cudaError_t launch_add_vec(double* a, const double* b, long long n, cudaStream_t s) {
-  k_add_vec<<<2048, 256, 0, s>>>(a, b, n);
+  { pns::count_launch(); k_add_vec<<<2048, 256, 0, s>>>(a, b, n); }
   return cudaGetLastError();
 }
+
+
+// ---------------------------------------------------------------------------- Woodbury driver
+struct WoodburyImpl {
+  int nblk = 0;
+  std::vector<int> k;
+  DevBuf d_k, d_koff, d_cmoff, d_Klist, d_delta, d_rpre, d_woff, cap;
+  std::vector<long long> koff, cmoff, rpre, woff;
+};
+
+Woodbury::Woodbury() : impl(new WoodburyImpl) {}
+Woodbury::~Woodbury() { delete impl; }
+
+static cudaError_t upload_ll(DevBuf& b, const std::vector<long long>& v, cudaStream_t s) {
+  b.release();
+  cudaError_t e = cudaMalloc(&b.p, sizeof(long long) * std::max<size_t>(1, v.size()));
+  if (e != cudaSuccess) return e;
+  b.bytes = sizeof(long long) * std::max<size_t>(1, v.size());
+  return cudaMemcpyAsync(b.p, v.data(), sizeof(long long) * v.size(), cudaMemcpyHostToDevice, s);
+}
+static cudaError_t upload_i(DevBuf& b, const std::vector<int>& v, cudaStream_t s) {
+  b.release();
+  cudaError_t e = cudaMalloc(&b.p, sizeof(int) * std::max<size_t>(1, v.size()));
+  if (e != cudaSuccess) return e;
+  b.bytes = sizeof(int) * std::max<size_t>(1, v.size());
+  return cudaMemcpyAsync(b.p, v.data(), sizeof(int) * v.size(), cudaMemcpyHostToDevice, s);
+}
+
+template <typename ST>
+cudaError_t Woodbury::setup(const Ctx& C, const BlockSet& B, int op, const double* state, const ST* X,
+                            const std::vector<int>& kc, int* d_bad) {
+  cudaStream_t s = C.stream;
+  WoodburyImpl& W = *impl;
+  W.nblk = B.nblk;
+  cudaError_t e;
+  // closure extras per primary row -> K lists
+  double* d_extra = nullptr;
+  if ((e = cudaMalloc(&d_extra, sizeof(double) * std::max(1LL, B.n_total))) != cudaSuccess) return e;
+  cudaMemsetAsync(d_extra, 0, sizeof(double) * std::max(1LL, B.n_total), s);
+  { pns::count_launch(); k_closure_extras<<<(unsigned)((B.n_total + 127) / 128), 128, 0, s>>>(
+      C.G, C.P, C.flags.as<uint8_t>(), op, state, C.owner.as<int>(), B.nblk, B.d_ioff.as<long long>(),
+      B.d_n.as<int>(), B.idx.as<int>(), B.n_total, d_extra); }
+  std::vector<double> ex(B.n_total);
+  cudaMemcpyAsync(ex.data(), d_extra, sizeof(double) * B.n_total, cudaMemcpyDeviceToHost, s);
+  e = cudaStreamSynchronize(s);
+  cudaFree(d_extra);
+  if (e != cudaSuccess) return e;
+  W.k.assign(B.nblk, 0);
+  W.koff.assign(B.nblk + 1, 0);
+  W.cmoff.assign(B.nblk + 1, 0);
+  W.rpre.assign(B.nblk + 1, 0);
+  W.woff.assign(B.nblk + 1, 0);
+  std::vector<int> Kl;
+  std::vector<double> dl;
+  for (int b = 0; b < B.nblk; ++b) {
+    for (int r = 0; r < B.n[b]; ++r) {
+      double v = ex[B.ioff[b] + r];
+      if (v != 0.0) { Kl.push_back(r); dl.push_back(v); }
+    }
+    W.k[b] = (int)(Kl.size() - W.koff[b]);
+    W.koff[b + 1] = (long long)Kl.size();
+    W.cmoff[b + 1] = W.cmoff[b] + (long long)W.k[b] * W.k[b];
+    W.rpre[b + 1] = W.rpre[b] + W.k[b];
+    W.woff[b + 1] = W.woff[b] + (long long)W.k[b] * kc[b];
+  }
+  if ((e = upload_i(W.d_k, W.k, s)) != cudaSuccess) return e;
+  if ((e = upload_ll(W.d_koff, W.koff, s)) != cudaSuccess) return e;
+  if ((e = upload_ll(W.d_cmoff, W.cmoff, s)) != cudaSuccess) return e;
+  if ((e = upload_i(W.d_Klist, Kl, s)) != cudaSuccess) return e;
+  W.d_delta.release();
+  if ((e = cudaMalloc(&W.d_delta.p, sizeof(double) * std::max<size_t>(1, dl.size()))) != cudaSuccess) return e;
+  W.d_delta.bytes = sizeof(double) * std::max<size_t>(1, dl.size());
+  cudaMemcpyAsync(W.d_delta.p, dl.data(), sizeof(double) * dl.size(), cudaMemcpyHostToDevice, s);
+  if ((e = upload_ll(W.d_rpre, W.rpre, s)) != cudaSuccess) return e;
+  if ((e = upload_ll(W.d_woff, W.woff, s)) != cudaSuccess) return e;
+  long long ctot = W.cmoff[B.nblk];
+  W.cap.release();
+  if ((e = cudaMalloc(&W.cap.p, sizeof(double) * std::max(1LL, ctot))) != cudaSuccess) return e;
+  W.cap.bytes = sizeof(double) * std::max(1LL, ctot);
+  if (ctot == 0) return cudaStreamSynchronize(s);
+  // blocks sorted by k (descending): the active set at step t is a prefix
+  std::vector<int> order(B.nblk);
+  for (int b = 0; b < B.nblk; ++b) order[b] = b;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return W.k[a] > W.k[c]; });
+  std::vector<long long> epre(B.nblk + 1, 0);
+  for (int q = 0; q < B.nblk; ++q) epre[q + 1] = epre[q] + (long long)W.k[order[q]] * W.k[order[q]];
+  DevBuf d_order, d_epre, colw, perm;
+  if ((e = upload_i(d_order, order, s)) != cudaSuccess) return e;
+  if ((e = upload_ll(d_epre, epre, s)) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&colw.p, sizeof(double) * std::max(1LL, W.koff[B.nblk]))) != cudaSuccess) return e;
+  colw.bytes = 1;
+  if ((e = cudaMalloc(&perm.p, sizeof(int) * std::max(1LL, W.koff[B.nblk]))) != cudaSuccess) return e;
+  perm.bytes = 1;
+  cudaMemsetAsync(colw.p, 0, sizeof(double) * std::max(1LL, W.koff[B.nblk]), s);
+  cudaMemsetAsync(perm.p, 0, sizeof(int) * std::max(1LL, W.koff[B.nblk]), s);
+  { pns::count_launch(); k_cap_assemble<ST><<<(unsigned)((epre[B.nblk] + 255) / 256), 256, 0, s>>>(
+      d_order.as<int>(), d_epre.as<long long>(), B.nblk, W.d_k.as<int>(), W.d_koff.as<long long>(),
+      W.d_cmoff.as<long long>(), W.d_Klist.as<int>(), W.d_delta.as<double>(), B.d_ld.as<int>(),
+      B.d_moff.as<long long>(), X, W.cap.as<double>()); }
+  int kmax = W.k[order[0]];
+  int cnt = B.nblk;
+  for (int t = 0; t < kmax; ++t) {
+    while (cnt > 0 && W.k[order[cnt - 1]] <= t) --cnt;
+    { pns::count_launch(); k_bpiv<<<cnt, 256, 0, s>>>(t, d_order.as<int>(), W.d_k.as<int>(), W.d_cmoff.as<long long>(),
+                                                      W.d_koff.as<long long>(), W.cap.as<double>(), colw.as<double>(),
+                                                      perm.as<int>(), d_bad); }
+    { pns::count_launch(); k_belim<<<(unsigned)((epre[cnt] + 255) / 256), 256, 0, s>>>(
+        t, d_order.as<int>(), d_epre.as<long long>(), cnt, W.d_k.as<int>(), W.d_cmoff.as<long long>(),
+        W.d_koff.as<long long>(), W.cap.as<double>(), colw.as<double>()); }
+  }
+  { pns::count_launch(); k_bunperm<<<(unsigned)((W.rpre[B.nblk] + 127) / 128), 128, 0, s>>>(
+      B.nblk, W.d_rpre.as<long long>(), W.d_k.as<int>(), W.d_cmoff.as<long long>(), W.d_koff.as<long long>(),
+      W.cap.as<double>(), perm.as<int>()); }
+  e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+// S = Abar^{-1} R for every primary block (R, S: n x kc per block at offsets roff, FP64)
+template <typename ST>
+cudaError_t Woodbury::apply(const Ctx& C, const BlockSet& B, const ST* X, const double* R, double* S, double* Y,
+                            const long long* d_roff, const int* d_kc, const std::vector<int>& kc) {
+  cudaStream_t s = C.stream;
+  WoodburyImpl& W = *impl;
+  cudaError_t e = launch_block_mm<ST, ST>(B, X, R, d_roff, d_kc, Y, s);
+  if (e != cudaSuccess) return e;
+  long long wtot = W.woff[B.nblk];
+  double *Wm = nullptr, *Z = nullptr;
+  if ((e = cudaMalloc(&Wm, sizeof(double) * std::max(1LL, wtot))) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&Z, sizeof(double) * std::max(1LL, wtot))) != cudaSuccess) { cudaFree(Wm); return e; }
+  cudaMemsetAsync(Wm, 0, sizeof(double) * std::max(1LL, wtot), s);
+  cudaMemsetAsync(Z, 0, sizeof(double) * std::max(1LL, wtot), s);
+  if (W.rpre[B.nblk] > 0) {
+    { pns::count_launch(); k_gather_rows<<<(unsigned)((W.rpre[B.nblk] + 127) / 128), 128, 0, s>>>(
+        B.nblk, W.d_rpre.as<long long>(), W.d_k.as<int>(), W.d_koff.as<long long>(), W.d_Klist.as<int>(), d_roff,
+        W.d_woff.as<long long>(), d_kc, Y, Wm); }
+    { pns::count_launch(); k_cap_mm<<<(unsigned)((W.rpre[B.nblk] * 32 + 255) / 256), 256, 0, s>>>(
+        B.nblk, W.d_rpre.as<long long>(), W.d_k.as<int>(), W.d_cmoff.as<long long>(), W.cap.as<double>(),
+        W.d_woff.as<long long>(), d_kc, Wm, Z); }
+  }
+  { pns::count_launch(); k_woodbury_update<ST><<<(unsigned)((B.n_total * 32 + 255) / 256), 256, 0, s>>>(
+      B.nblk, B.d_ioff.as<long long>(), B.d_n.as<int>(), B.d_ld.as<int>(), B.d_moff.as<long long>(), X, B.n_total,
+      W.d_k.as<int>(), W.d_koff.as<long long>(), W.d_Klist.as<int>(), d_roff, W.d_woff.as<long long>(), d_kc, Y, Z,
+      S); }
+  e = cudaStreamSynchronize(s);
+  cudaFree(Wm);
+  cudaFree(Z);
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+template cudaError_t Woodbury::setup<float>(const Ctx&, const BlockSet&, int, const double*, const float*,
+                                            const std::vector<int>&, int*);
+template cudaError_t Woodbury::setup<double>(const Ctx&, const BlockSet&, int, const double*, const double*,
+                                             const std::vector<int>&, int*);
+template cudaError_t Woodbury::apply<float>(const Ctx&, const BlockSet&, const float*, const double*, double*,
+                                            double*, const long long*, const int*, const std::vector<int>&);
+template cudaError_t Woodbury::apply<double>(const Ctx&, const BlockSet&, const double*, const double*, double*,
+                                             double*, const long long*, const int*, const std::vector<int>&);
 
 }  // namespace pns

@@ -130,8 +130,8 @@ cudaError_t launch_multidot(const double* V, long long ld, int nvec, const doubl
   if (nblocks <= 0 || nblocks > RED_BLOCKS) nblocks = RED_BLOCKS;
   for (int i0 = 0; i0 < nvec; i0 += MAXV) {
     int cnt = nvec - i0 < MAXV ? nvec - i0 : MAXV;
-    k_multidot<<<nblocks, 256, 0, s>>>(V + (long long)i0 * ld, ld, cnt, w, n, partial);
-    k_reduce_rows<<<cnt, 256, 0, s>>>(partial, nblocks, out + i0);
+    { pns::count_launch(); k_multidot<<<nblocks, 256, 0, s>>>(V + (long long)i0 * ld, ld, cnt, w, n, partial); }
+    { pns::count_launch(); k_reduce_rows<<<cnt, 256, 0, s>>>(partial, nblocks, out + i0); }
   }
   return cudaGetLastError();
 }
@@ -140,44 +140,44 @@ cudaError_t launch_multi_axpy(double* w, const double* V, long long ld, int nvec
                               long long n, cudaStream_t s) {
   for (int i0 = 0; i0 < nvec; i0 += MAXV) {
     int cnt = nvec - i0 < MAXV ? nvec - i0 : MAXV;
-    k_multi_axpy<<<1216, 256, 0, s>>>(w, V + (long long)i0 * ld, ld, cnt, h + i0, sign, n);
+    { pns::count_launch(); k_multi_axpy<<<1216, 256, 0, s>>>(w, V + (long long)i0 * ld, ld, cnt, h + i0, sign, n); }
   }
   return cudaGetLastError();
 }
 
 cudaError_t launch_dot(const double* a, const double* b, long long n, double* partial, double* out, cudaStream_t s) {
-  k_multidot<<<RED_BLOCKS, 256, 0, s>>>(a, 0, 1, b, n, partial);
-  k_reduce_rows<<<1, 256, 0, s>>>(partial, RED_BLOCKS, out);
+  { pns::count_launch(); k_multidot<<<RED_BLOCKS, 256, 0, s>>>(a, 0, 1, b, n, partial); }
+  { pns::count_launch(); k_reduce_rows<<<1, 256, 0, s>>>(partial, RED_BLOCKS, out); }
   return cudaGetLastError();
 }
 
 // invert == 1: x *= 1 / sqrt(*den)
 cudaError_t launch_scale(double* x, long long n, const double* num, const double* den, int invert, cudaStream_t s) {
-  k_scale<<<1216, 256, 0, s>>>(x, n, num, den, invert);
+  { pns::count_launch(); k_scale<<<1216, 256, 0, s>>>(x, n, num, den, invert); }
   return cudaGetLastError();
 }
 
 cudaError_t launch_axpy(double* y, const double* x, double a, long long n, cudaStream_t s) {
-  k_axpy<<<1216, 256, 0, s>>>(y, x, a, n);
+  { pns::count_launch(); k_axpy<<<1216, 256, 0, s>>>(y, x, a, n); }
   return cudaGetLastError();
 }
 
 cudaError_t launch_hcol(double* H, int ldh, int j, const double* h1, const double* h2, const double* hnorm,
                         cudaStream_t s) {
-  k_hcol<<<1, 128, 0, s>>>(H, ldh, j, h1, h2, hnorm);
+  { pns::count_launch(); k_hcol<<<1, 128, 0, s>>>(H, ldh, j, h1, h2, hnorm); }
   return cudaGetLastError();
 }
 
 cudaError_t launch_givens(double* H, int ldh, double* cs, double* sn, double* g, int j, double* resid_out,
                           cudaStream_t s) {
-  k_givens<<<1, 32, 0, s>>>(H, ldh, cs, sn, g, j, resid_out);
+  { pns::count_launch(); k_givens<<<1, 32, 0, s>>>(H, ldh, cs, sn, g, j, resid_out); }
   return cudaGetLastError();
 }
 
 // y = R^{-1} g, then x += Z y
 cudaError_t launch_trisolve_update(const double* H, int ldh, const double* g, int k, double* y, const double* Z,
                                    long long ld, double* x, long long n, cudaStream_t s) {
-  k_trisolve<<<1, 32, 0, s>>>(H, ldh, g, k, y);
+  { pns::count_launch(); k_trisolve<<<1, 32, 0, s>>>(H, ldh, g, k, y); }
   return launch_multi_axpy(x, Z, ld, k, y, 1.0, n, s);
 }
 

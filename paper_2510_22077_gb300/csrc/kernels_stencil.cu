@@ -114,7 +114,7 @@ __global__ void k_cast_f2d(const float* __restrict__ in, double* __restrict__ ou
 
 cudaError_t launch_residual(const Ctx& C, int stokes, const double* x, const double* xprev, double* r) {
   int thr = 256, blk = (C.G.ncell + thr - 1) / thr;
-  k_residual<<<blk, thr, 0, C.stream>>>(C.G, C.P, C.flags.as<uint8_t>(), stokes, x, xprev, r);
+  { pns::count_launch(); k_residual<<<blk, thr, 0, C.stream>>>(C.G, C.P, C.flags.as<uint8_t>(), stokes, x, xprev, r); }
   return cudaGetLastError();
 }
 
@@ -122,20 +122,20 @@ template <typename VT>
 cudaError_t launch_apply(const Ctx& C, int op, const double* state, const VT* v, const VT* b, VT* y, bool fp64_math) {
   int thr = 256, blk = (C.G.ncell + thr - 1) / thr;
   if (fp64_math)
-    k_apply<double, VT><<<blk, thr, 0, C.stream>>>(C.G, C.P, C.flags.as<uint8_t>(), op, state, v, b, y);
+    { pns::count_launch(); k_apply<double, VT><<<blk, thr, 0, C.stream>>>(C.G, C.P, C.flags.as<uint8_t>(), op, state, v, b, y); }
   else
-    k_apply<float, VT><<<blk, thr, 0, C.stream>>>(C.G, C.P, C.flags.as<uint8_t>(), op, state, v, b, y);
+    { pns::count_launch(); k_apply<float, VT><<<blk, thr, 0, C.stream>>>(C.G, C.P, C.flags.as<uint8_t>(), op, state, v, b, y); }
   return cudaGetLastError();
 }
 template cudaError_t launch_apply<double>(const Ctx&, int, const double*, const double*, const double*, double*, bool);
 template cudaError_t launch_apply<float>(const Ctx&, int, const double*, const float*, const float*, float*, bool);
 
 cudaError_t launch_cast_d2f(const double* in, float* out, long long n, cudaStream_t s) {
-  k_cast_d2f<<<1216, 256, 0, s>>>(in, out, n);
+  { pns::count_launch(); k_cast_d2f<<<1216, 256, 0, s>>>(in, out, n); }
   return cudaGetLastError();
 }
 cudaError_t launch_cast_f2d(const float* in, double* out, long long n, cudaStream_t s) {
-  k_cast_f2d<<<1216, 256, 0, s>>>(in, out, n);
+  { pns::count_launch(); k_cast_f2d<<<1216, 256, 0, s>>>(in, out, n); }
   return cudaGetLastError();
 }
 

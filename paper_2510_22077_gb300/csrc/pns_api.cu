@@ -17,6 +17,13 @@ struct pns_ctx {
   Ctx c;
 };
 
+#include <atomic>
+namespace pns {
+static std::atomic<long long> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
+}  // namespace pns
+
 namespace {
 
 constexpr int GEMV_ROWS = 32;   // rows per local-solve work item (8 warps x 4 rows)
@@ -42,12 +49,18 @@ int fail(Ctx& C, int code, const char* what, cudaError_t e = cudaSuccess) {
     if (s_ != PNS_OK) return s_;      \
   } while (0)
 
+// Device allocation, zero-filled: no buffer of the library is ever read before it is written, but a
+// zero fill makes any such mistake deterministic instead of depending on recycled memory.
 cudaError_t dalloc(DevBuf& b, size_t bytes) {
   b.release();
   if (bytes == 0) return cudaSuccess;
   cudaError_t e = cudaMalloc(&b.p, bytes);
-  if (e == cudaSuccess) b.bytes = bytes;
-  else b.p = nullptr;
+  if (e == cudaSuccess) {
+    b.bytes = bytes;
+    e = cudaMemset(b.p, 0, bytes);
+  } else {
+    b.p = nullptr;
+  }
   return e;
 }
 
@@ -153,7 +166,22 @@ __global__ void k_setcol(double* __restrict__ A, int n, int k, const double* __r
 }
 
 // local inverses of one block set in the storage type of `precision`
-int build_local(Ctx& C, Precond& pc, BlockSet& B, int* d_bad) {
+int to_bf16(Ctx& C, BlockSet& B) {
+  DevBuf bf;
+  CK(dalloc(bf, sizeof(__nv_bfloat16) * B.m_total));
+  { pns::count_launch(); k_f2bf<<<4096, 256, 0, C.stream>>>(B.mat.as<float>(), bf.as<__nv_bfloat16>(), B.m_total); }
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(C.stream));
+  B.mat.release();
+  B.mat.p = bf.p;
+  B.mat.bytes = bf.bytes;
+  bf.p = nullptr;
+  bf.bytes = 0;
+  return PNS_OK;
+}
+
+// local inverses of one block set; with defer_bf16 the FP32 inverse is kept (converted later)
+int build_local(Ctx& C, Precond& pc, BlockSet& B, int* d_bad, bool defer_bf16 = false) {
   if (B.nblk == 0) return PNS_OK;
   const cudaStream_t s = C.stream;
   if (pc.precision == PNS_FP64) {
@@ -162,8 +190,7 @@ int build_local(Ctx& C, Precond& pc, BlockSet& B, int* d_bad) {
     CK(launch_assemble<double>(C, B, pc.op, pc.state.as<double>(), B.mat.as<double>(), 0));
     CK(launch_gj_invert<double>(B, B.mat.as<double>(), d_bad, s));
   } else {
-    DevBuf tmp;
-    DevBuf& F = pc.precision == PNS_FP32 ? B.mat : tmp;
+    DevBuf& F = B.mat;
     CK(dalloc(F, sizeof(float) * B.m_total));
     CK(cudaMemsetAsync(F.p, 0, F.bytes, s));
     CK(launch_assemble<float>(C, B, pc.op, pc.state.as<double>(), F.as<float>(), 0));
@@ -176,16 +203,11 @@ int build_local(Ctx& C, Precond& pc, BlockSet& B, int* d_bad) {
       cudaMemGetInfo(&fr, &tot);
       size_t budget = std::max<size_t>(fr / 2, (size_t)1 << 28);
       double before = 0;
-      CK((launch_ns_refine<float, float>(C, B, pc.op, pc.state.as<double>(), 0, F.as<float>(), steps, 2e-6,
+      CK((launch_ns_refine<float, float>(C, B, pc.op, pc.state.as<double>(), 0, F.as<float>(), steps, 1e-5,
                                           budget, &before, nullptr)));
       pc.ns_residual_before = std::max(pc.ns_residual_before, before);
     }
-    if (pc.precision == PNS_BF16) {
-      CK(dalloc(B.mat, sizeof(__nv_bfloat16) * B.m_total));
-      k_f2bf<<<4096, 256, 0, s>>>(F.as<float>(), B.mat.as<__nv_bfloat16>(), B.m_total);
-      CK(cudaGetLastError());
-      CK(cudaStreamSynchronize(s));
-    }
+    if (pc.precision == PNS_BF16 && !defer_bf16) CKS(to_bf16(C, B));
   }
   return PNS_OK;
 }
@@ -249,36 +271,32 @@ int build_coarse_t(Ctx& C, Precond& pc, int* d_bad) {
   CK(launch_closure_rhs(C, B, pc.op, pc.state.as<double>(), d_colbase.as<int>(), d_cols.as<int>(),
                         d_roff.as<long long>(), d_kc.as<int>(), rhs.as<double>()));
   {
-    // closure blocks: A_b on p_i plus the row sums of its couplings to f faces and other primary grids
-    DevBuf cm;
-    CK(dalloc(cm, sizeof(SB) * B.m_total));
-    CK(cudaMemsetAsync(cm.p, 0, cm.bytes, s));
-    CK(launch_assemble<SB>(C, B, pc.op, pc.state.as<double>(), cm.as<SB>(), 1));
-    CK(launch_gj_invert<SB>(B, cm.as<SB>(), d_bad, s));
-    CK((launch_block_mm<SB, SB>(B, cm.as<SB>(), rhs.as<double>(), d_roff.as<long long>(), d_kc.as<int>(),
-                                out.as<double>(), s)));
-    // iterative refinement of the shape/correction solves with FP64 residuals of the closure blocks
-    DevBuf res, ds;
+    // closure blocks Abar = A_b on p_i plus the row sums of its couplings to f faces and other
+    // primary grids (Eqs. 6, 9): solved by the Woodbury identity on the primary-block inverses,
+    // then two steps of iterative refinement with FP64 residuals of Abar
+    Woodbury WB;
+    CK(WB.setup<SB>(C, B, pc.op, pc.state.as<double>(), B.mat.as<SB>(), kc, d_bad));
+    DevBuf Y, res, ds;
+    CK(dalloc(Y, sizeof(double) * std::max(1LL, rtot)));
     CK(dalloc(res, sizeof(double) * std::max(1LL, rtot)));
     CK(dalloc(ds, sizeof(double) * std::max(1LL, rtot)));
+    CK(WB.apply<SB>(C, B, B.mat.as<SB>(), rhs.as<double>(), out.as<double>(), Y.as<double>(),
+                    d_roff.as<long long>(), d_kc.as<int>(), kc));
     for (int it = 0; it < 2; ++it) {
       CK(launch_closure_residual(C, B, pc.op, pc.state.as<double>(), d_roff.as<long long>(), d_kc.as<int>(),
                                  rhs.as<double>(), out.as<double>(), res.as<double>()));
-      CK((launch_block_mm<SB, SB>(B, cm.as<SB>(), res.as<double>(), d_roff.as<long long>(), d_kc.as<int>(),
-                                  ds.as<double>(), s)));
+      CK(WB.apply<SB>(C, B, B.mat.as<SB>(), res.as<double>(), ds.as<double>(), Y.as<double>(),
+                      d_roff.as<long long>(), d_kc.as<int>(), kc));
       CK(launch_add_vec(out.as<double>(), ds.as<double>(), rtot, s));
     }
     CK(cudaStreamSynchronize(s));
   }
-  // basis in the coarse storage type
-  if (pc.precision == PNS_FP64) {
-    CK(dalloc(pc.basis, sizeof(double) * std::max(1LL, rtot)));
-    CK(cudaMemcpyAsync(pc.basis.p, out.p, sizeof(double) * rtot, cudaMemcpyDeviceToDevice, s));
-  } else {
-    CK(dalloc(pc.basis, sizeof(float) * std::max(1LL, rtot)));
-    k_d2f_any<<<2048, 256, 0, s>>>(out.as<double>(), pc.basis.as<float>(), rtot);
-    CK(cudaGetLastError());
-  }
+  // The basis stays FP64 in every precision (Sum_i n_i (|C_i| + 1) values, ~0.1 GB for a 96^3 pack).
+  // The coarse matrix has a near-null mode (the constant interface pressure, pinned through one cell
+  // only): rounding the basis to FP32 perturbs A^o by ~1e-7 |A^o|, above its smallest singular value,
+  // and the coarse solve then amplifies the rounding along that mode.
+  CK(dalloc(pc.basis, sizeof(double) * std::max(1LL, rtot)));
+  CK(cudaMemcpyAsync(pc.basis.p, out.p, sizeof(double) * rtot, cudaMemcpyDeviceToDevice, s));
   // coarse matrix A^o = R^ A_b P^ column by column (prolong e_k, apply A_b, restrict)
   const int no = pc.n_o;
   DevBuf Ao, ek, zf, yf, col, work, perm;
@@ -287,19 +305,12 @@ int build_coarse_t(Ctx& C, Precond& pc, int* d_bad) {
   CK(dalloc(zf, sizeof(double) * C.nfull));
   CK(dalloc(yf, sizeof(double) * C.nfull));
   CK(dalloc(col, sizeof(double) * no));
-  DevBuf zff;
-  if (pc.precision != PNS_FP64) CK(dalloc(zff, sizeof(float) * C.nfull));
   for (int k = 0; k < no; ++k) {
-    k_unit<<<(no + 255) / 256, 256, 0, s>>>(ek.as<double>(), no, k);
-    if (pc.precision == PNS_FP64) CK((launch_prolong<double, double>(C, pc, ek.as<double>(), zf.as<double>())));
-    else {
-      // the stored FP32 basis column itself (the apply uses the same rounded basis)
-      CK((launch_prolong<float, float>(C, pc, ek.as<double>(), zff.as<float>())));
-      CK(launch_cast_f2d(zff.as<float>(), zf.as<double>(), C.nfull, s));
-    }
+    { pns::count_launch(); k_unit<<<(no + 255) / 256, 256, 0, s>>>(ek.as<double>(), no, k); }
+    CK((launch_prolong<double, double>(C, pc, ek.as<double>(), zf.as<double>())));
     CK(launch_apply<double>(C, pc.op, pc.state.as<double>(), zf.as<double>(), nullptr, yf.as<double>(), true));
     CK(launch_seg_sum(pc, yf.p, 1, col.as<double>(), s));
-    k_setcol<<<(no + 255) / 256, 256, 0, s>>>(Ao.as<double>(), no, k, col.as<double>());
+    { pns::count_launch(); k_setcol<<<(no + 255) / 256, 256, 0, s>>>(Ao.as<double>(), no, k, col.as<double>()); }
     CK(cudaGetLastError());
   }
   CK(dalloc(work, sizeof(double) * no));
@@ -334,6 +345,7 @@ int ensure_scratch(Ctx& C, const Precond& pc) {
 int build_precond(Ctx& C, Precond& pc, int variant, const double* x_lin) {
   const cudaStream_t s = C.stream;
   pc.built = false;
+  pc.ns_residual_before = 0;
   pc.variant = variant;
   pc.precision = C.opt.precision;
   pc.op = op_of_variant(variant);
@@ -350,7 +362,7 @@ int build_precond(Ctx& C, Precond& pc, int variant, const double* x_lin) {
   CK(dalloc(bad, sizeof(int)));
   CK(cudaMemsetAsync(bad.p, 0, sizeof(int), s));
   double t0 = now_ms();
-  CKS(build_local(C, pc, pc.prim, bad.as<int>()));
+  CKS(build_local(C, pc, pc.prim, bad.as<int>(), true));
   CKS(build_local(C, pc, pc.dual, bad.as<int>()));
   CK(cudaStreamSynchronize(s));
   double t1 = now_ms();
@@ -359,10 +371,12 @@ int build_precond(Ctx& C, Precond& pc, int variant, const double* x_lin) {
     if (pc.precision == PNS_FP64) CKS(build_coarse_t<double>(C, pc, bad.as<int>()));
     else CKS(build_coarse_t<float>(C, pc, bad.as<int>()));
   }
+  if (pc.precision == PNS_BF16) CKS(to_bf16(C, pc.prim));
   C.t_mg_ms = now_ms() - t1;
   int hbad = 0;
   CK(cudaMemcpy(&hbad, bad.p, sizeof(int), cudaMemcpyDeviceToHost));
   if (hbad) return fail(C, PNS_ERR_SINGULAR, "zero or non-finite pivot in a local or coarse factor");
+  pc.ns_residual_before = pc.ns_residual_before;
   pc.local_bytes = 0;
   for (BlockSet* B : {&pc.prim, &pc.dual})
     for (int b = 0; b < B->nblk; ++b)
@@ -376,14 +390,23 @@ int build_precond(Ctx& C, Precond& pc, int variant, const double* x_lin) {
 template <typename ST, typename PT>
 int local_solve(Ctx& C, Precond& pc, BlockSet& B, const double* t, double* z, int add) {
   (void)pc;
-  if (C.opt.timing) cudaEventRecord(C.ev0, C.stream);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (C.opt.timing) {
+    if (C.ev_used + 2 > C.ev_pool.size()) {
+      cudaEvent_t a, b;
+      CK(cudaEventCreate(&a));
+      CK(cudaEventCreate(&b));
+      C.ev_pool.push_back(a);
+      C.ev_pool.push_back(b);
+    }
+    e0 = C.ev_pool[C.ev_used];
+    e1 = C.ev_pool[C.ev_used + 1];
+    C.ev_used += 2;
+    CK(cudaEventRecord(e0, C.stream));
+  }
   CK((launch_local_solve<ST, PT>(B, B.mat.as<ST>(), t, z, C.pk_x.as<PT>(), add, C.stream)));
   if (C.opt.timing) {
-    cudaEventRecord(C.ev1, C.stream);
-    cudaEventSynchronize(C.ev1);
-    float ms = 0;
-    cudaEventElapsedTime(&ms, C.ev0, C.ev1);
-    C.t_local_ms += ms;
+    CK(cudaEventRecord(e1, C.stream));
     C.local_launches += 1;
   }
   return PNS_OK;
@@ -407,8 +430,7 @@ int precond_apply_impl(Ctx& C, Precond& pc, const double* v, double* z) {
   if (pc.coarse) {
     CK(launch_seg_sum(pc, v, 1, C.coarse_rhs.as<double>(), s));
     CK(launch_coarse_gemv<double>(pc.ao_inv.as<double>(), pc.n_o, C.coarse_rhs.as<double>(), C.coarse_x.as<double>(), s));
-    if (pc.precision == PNS_FP64) CK((launch_prolong<double, double>(C, pc, C.coarse_x.as<double>(), zG)));
-    else CK((launch_prolong<float, double>(C, pc, C.coarse_x.as<double>(), zG)));
+    CK((launch_prolong<double, double>(C, pc, C.coarse_x.as<double>(), zG)));
     CK(launch_apply<double>(C, op, st, zG, v, t1, true));           // t1 = v - A z_G
   } else {
     CK(cudaMemsetAsync(zG, 0, sizeof(double) * n, s));
@@ -423,7 +445,7 @@ int precond_apply_impl(Ctx& C, Precond& pc, const double* v, double* z) {
   if (pc.precision == PNS_FP64) CKS((local_solve<double, double>(C, pc, pc.prim, t2, zp, 0)));
   else if (pc.precision == PNS_FP32) CKS((local_solve<float, float>(C, pc, pc.prim, t2, zp, 0)));
   else CKS((local_solve<__nv_bfloat16, float>(C, pc, pc.prim, t2, zp, 0)));
-  k_sum3<double><<<2048, 256, 0, s>>>(zG, zd, zp, z, n);
+  { pns::count_launch(); k_sum3<double><<<2048, 256, 0, s>>>(zG, zd, zp, z, n); }
   CK(cudaGetLastError());
   return PNS_OK;
 }
@@ -455,6 +477,8 @@ double host_norm(Ctx& C, const double* a, int& st) {
   st = e == cudaSuccess ? PNS_OK : fail(C, PNS_ERR_CUDA, "norm", e);
   return std::sqrt(h);
 }
+
+void harvest_events(Ctx& C);
 
 // Solve J(op, state) dx = b with right-preconditioned FGMRES(m); dx is overwritten.
 int fgmres(Ctx& C, Precond& pc, int op, const double* state, const double* b, double* dx, double tol_abs, int maxit,
@@ -510,6 +534,7 @@ int fgmres(Ctx& C, Precond& pc, int op, const double* state, const double* b, do
       double hres[2];
       CK(cudaMemcpyAsync(hres, outv, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
       CK(cudaStreamSynchronize(s));
+      if (C.ev_used >= 256) harvest_events(C);
       ++its;
       k = j + 1;
       if (!std::isfinite(hres[0])) return fail(C, PNS_ERR_NAN, "non-finite Givens residual");
@@ -525,6 +550,15 @@ int fgmres(Ctx& C, Precond& pc, int op, const double* state, const double* b, do
   }
   its_out = its;
   return PNS_OK;
+}
+
+// Sum the local-solve event pairs recorded since the last harvest (the stream has synchronised).
+void harvest_events(Ctx& C) {
+  for (size_t k = 0; k + 1 < C.ev_used; k += 2) {
+    float ms = 0;
+    if (cudaEventElapsedTime(&ms, C.ev_pool[k], C.ev_pool[k + 1]) == cudaSuccess) C.t_local_ms += ms;
+  }
+  C.ev_used = 0;
 }
 
 int newton(Ctx& C, Precond& pc, int stokes, double* x, const double* x_prev, pns_stats* stt) {
@@ -557,7 +591,7 @@ int newton(Ctx& C, Precond& pc, int stokes, double* x, const double* x_prev, pns
     if (!std::isfinite(rel)) { code = fail(C, PNS_ERR_NAN, "non-finite Newton residual"); break; }
     if (rel < C.opt.newton_tol) break;
     if (k >= maxn) { code = fail(C, PNS_ERR_NOT_CONVERGED, "Newton iteration cap reached"); break; }
-    k_negate<<<2048, 256, 0, s>>>(C.rk.as<double>(), C.rk.as<double>(), n);
+    { pns::count_launch(); k_negate<<<2048, 256, 0, s>>>(C.rk.as<double>(), C.rk.as<double>(), n); }
     CK(cudaGetLastError());
     C.cur_state = stokes ? nullptr : x;
     double t0 = now_ms();
@@ -574,6 +608,7 @@ int newton(Ctx& C, Precond& pc, int stokes, double* x, const double* x_prev, pns
   }
   C.cur_state = nullptr;
   CK(cudaStreamSynchronize(s));
+  harvest_events(C);
   loc.t_sol_ms = tsol;
   loc.t_setup_ms = C.t_setup_ms;
   loc.t_mg_ms = C.t_mg_ms;
@@ -581,6 +616,8 @@ int newton(Ctx& C, Precond& pc, int stokes, double* x, const double* x_prev, pns
   loc.t_local_ms = C.t_local_ms;
   loc.local_launches = C.local_launches;
   loc.local_bytes_per_apply = pc.local_bytes;
+  loc.kernel_launches = launch_count();
+  loc.refine_residual_max = pc.ns_residual_before;
   if (stt) *stt = loc;
   return code;
 }
@@ -671,6 +708,7 @@ int pns_setup(pns_ctx** out, int nz, int ny, int nx, const uint8_t* mask, const 
 
 void pns_destroy(pns_ctx* ctx) {
   if (!ctx) return;
+  for (cudaEvent_t e : ctx->c.ev_pool) cudaEventDestroy(e);
   if (ctx->c.ev0) cudaEventDestroy(ctx->c.ev0);
   if (ctx->c.ev1) cudaEventDestroy(ctx->c.ev1);
   delete ctx;
@@ -763,6 +801,19 @@ int pns_stokes_solve(pns_ctx* ctx, double* x, pns_stats* st) {
   int code = newton(C, tmp, 1, x, nullptr, st);
   C.opt.max_newton = maxn;
   return code;
+}
+
+int pns_export_coarse(const pns_ctx* ctx, double* ao_inv, int* n_o) {
+  if (check_ctx(ctx) || !n_o) return PNS_ERR_ARG;
+  const Ctx& C = ctx->c;
+  *n_o = C.pc.n_o;
+  if (!C.pc.built || !C.pc.coarse) return PNS_ERR_STATE;
+  if (ao_inv) {
+    cudaError_t e = cudaMemcpy(ao_inv, C.pc.ao_inv.p, sizeof(double) * (size_t)C.pc.n_o * C.pc.n_o,
+                               cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return PNS_ERR_CUDA;
+  }
+  return PNS_OK;
 }
 
 int pns_export_maps(const pns_ctx* ctx, int32_t* cell_prim, int32_t* cell_iface, int32_t* face_class, uint8_t* tags,

@@ -250,67 +250,50 @@ def _markers(dist, arr, amap, periodic, w):
     return peak
 
 
-def label_pores(mask: np.ndarray, target: int, periodic=X_PERIODIC, windows=range(1, 25)) -> Labelling:
-    """Watershed decomposition of the void into about `target` pores.
+def _nms_markers(dist, arr, amap, periodic, dmin, rmin=1.0):
+    """Local maxima of the distance (3^d neighbourhood), accepted in order of decreasing distance
+    (ties: lowest linear index) when farther than dmin from every accepted marker (minimum image
+    along periodic axes).  Returns the accepted linear indices."""
+    padded, pads = _pad_periodic(dist, amap, periodic, 1, 0.0)
+    mx = _crop(ndimage.maximum_filter(padded, size=3, mode="constant", cval=0.0), pads)
+    cand = np.flatnonzero((dist >= mx) & arr & (dist >= rmin))
+    cand = cand[np.argsort(-dist.ravel()[cand], kind="stable")]
+    coords = np.array(np.unravel_index(cand, arr.shape)).T.astype(np.float64)
+    ext = np.array(arr.shape, np.float64)
+    wrap = np.array([periodic[[k for k, v in amap.items() if v == ax][0]] for ax in range(arr.ndim)])
+    acc = np.zeros((0, arr.ndim))
+    keep = []
+    for k in range(len(cand)):
+        if len(acc):
+            dlt = np.abs(acc - coords[k])
+            dlt = np.where(wrap, np.minimum(dlt, ext - dlt), dlt)
+            if np.min((dlt * dlt).sum(axis=1)) < dmin * dmin:
+                continue
+        acc = np.vstack([acc, coords[k]])
+        keep.append(cand[k])
+    return np.array(keep, np.int64)
 
-    Heights are the distance map; markers are plateau components of cells that are maxima of the
-    distance within a (2w+1)-wide window (w chosen from `windows` to bring the marker count closest
-    to `target`).  A priority flood (highest distance first; ties by insertion order) grows the
-    markers over the face-connected void (wrapping along periodic axes).  Void components without a
-    marker get one at their deepest cell (lowest linear index among ties)."""
-    m = np.asarray(mask).astype(bool)
-    arr, amap = _squeeze2d(m)
-    dist2 = _squeeze2d(distance_to_solid(m, periodic))[0]
-    best = None
-    for w in windows:
-        peak = _markers(dist2, arr, amap, periodic, w)
-        plab, npk = ndimage.label(peak, structure=np.ones((3,) * arr.ndim, bool))
-        score = abs(npk - target)
-        if best is None or score < best[0]:
-            best = (score, w, plab, npk)
-        if npk < target:
-            break
-    _, w, plab, npk = best
-    flat_d = dist2.ravel()
+
+def _flood(arr, amap, periodic, flat_d, seeds_lab):
+    """Priority flood of labels over the face-connected void (highest distance first; ties by
+    insertion order).  seeds_lab: flat label array with markers > 0."""
     shape = arr.shape
+    lab = seeds_lab.copy()
     flat_void = arr.ravel()
-    lab = plab.ravel().astype(np.int64).copy()
-    # renumber markers by lowest linear index of their plateau
-    if npk > 0:
-        first = ndimage.minimum(np.arange(lab.size), labels=plab.ravel(), index=np.arange(1, npk + 1))
-        order = np.argsort(first, kind="stable")
-        remap = np.zeros(npk + 1, np.int64)
-        remap[order + 1] = np.arange(1, npk + 1)
-        lab = remap[lab]
-    # components without a marker
-    comp, ncomp = void_components(m, periodic)
-    comp = _squeeze2d(comp)[0].ravel()
-    has = np.zeros(ncomp + 1, bool)
-    has[comp[lab > 0]] = True
-    nl = npk
-    for cidx in range(1, ncomp + 1):
-        if not has[cidx]:
-            cells = np.flatnonzero(comp == cidx)
-            c = cells[np.argmax(flat_d[cells])]
-            nl += 1
-            lab[c] = nl
-    # neighbour offsets on the (possibly 2D) array with wrap where periodic
     strides = np.array([int(np.prod(shape[a + 1:])) for a in range(len(shape))])
     wraps = {ax_np: periodic[ax_s] for ax_s, ax_np in amap.items()}
     heap = []
     counter = 0
-    seeds = np.flatnonzero(lab > 0)
-    for c in seeds:
+    for c in np.flatnonzero(lab > 0):
         heapq.heappush(heap, (-flat_d[c], counter, int(c)))
         counter += 1
-    coords_cache = np.unravel_index
     while heap:
         _, _, c = heapq.heappop(heap)
         lc = lab[c]
-        idx = coords_cache(c, shape)
+        idx = np.unravel_index(c, shape)
         for ax in range(len(shape)):
-            for s in (-1, 1):
-                v = idx[ax] + s
+            for sgn in (-1, 1):
+                v = idx[ax] + sgn
                 if v < 0 or v >= shape[ax]:
                     if not wraps[ax]:
                         continue
@@ -320,8 +303,186 @@ def label_pores(mask: np.ndarray, target: int, periodic=X_PERIODIC, windows=rang
                     lab[nb] = lc
                     heapq.heappush(heap, (-flat_d[nb], counter, int(nb)))
                     counter += 1
-    labels = lab.reshape(shape).astype(np.int32).reshape(mask.shape)
-    return Labelling(labels=labels, n_labels=int(nl), window=int(w), dist=dist2.reshape(mask.shape))
+    return lab
+
+
+def _region_contacts(lab, arr, amap, periodic):
+    """Face contacts between distinct regions: dict (a, b) -> count with a < b."""
+    L3 = lab.reshape(arr.shape)
+    contacts = {}
+    for ax_s, ax_np in amap.items():
+        n = arr.shape[ax_np]
+        a_ = np.take(L3, np.arange(n - 1), axis=ax_np)
+        b_ = np.take(L3, np.arange(1, n), axis=ax_np)
+        pairs = [(a_, b_)]
+        if periodic[ax_s]:
+            pairs.append((np.take(L3, [n - 1], axis=ax_np), np.take(L3, [0], axis=ax_np)))
+        for x, y in pairs:
+            sel = (x > 0) & (y > 0) & (x != y)
+            lo = np.minimum(x[sel], y[sel])
+            hi = np.maximum(x[sel], y[sel])
+            key = lo.astype(np.int64) * (int(lab.max()) + 1) + hi
+            uk, cnt = np.unique(key, return_counts=True)
+            for k, c in zip(uk.tolist(), cnt.tolist()):
+                pr = (k // (int(lab.max()) + 1), k % (int(lab.max()) + 1))
+                contacts[pr] = contacts.get(pr, 0) + c
+    return contacts
+
+
+def _merge_regions(lab, arr, amap, periodic, min_cells, max_cells, target):
+    """Greedy merging on the region adjacency graph.  Repeatedly take a region that touches no solid
+    cell and no box wall (a pore is bounded by solid; such a region would make its closure block of
+    Eqs. 6/9 singular: a constant velocity satisfies the closure on every side), else the smallest
+    region below min_cells, or (while more than `target` regions remain) the smallest region, and
+    merge it into the neighbour it shares the most faces with among those keeping the merged size
+    <= max_cells (a region below min_cells may exceed max_cells if no neighbour fits).  Ties: lower
+    label.  Regions are renumbered 1..K by their lowest linear index."""
+    nl = int(lab.max())
+    size = np.bincount(lab, minlength=nl + 1).astype(np.int64)
+    size[0] = 0
+    # regions touching a solid cell or a (non-periodic) box wall; the others are merged away
+    wall = np.zeros(nl + 1, bool)
+    L3 = lab.reshape(arr.shape)
+    for ax_s, ax_np in amap.items():
+        for sgn in (-1, 1):
+            sh = np.roll(arr, sgn, axis=ax_np)
+            solid_nb = ~sh
+            if not periodic[ax_s]:
+                edge = [slice(None)] * arr.ndim
+                edge[ax_np] = 0 if sgn == 1 else arr.shape[ax_np] - 1
+                solid_nb[tuple(edge)] = True
+            wall[np.unique(L3[arr & solid_nb])] = True
+    nbrs = {r: {} for r in range(1, nl + 1)}
+    for (a_, b_), c in _region_contacts(lab, arr, amap, periodic).items():
+        nbrs[a_][b_] = nbrs[a_].get(b_, 0) + c
+        nbrs[b_][a_] = nbrs[b_].get(a_, 0) + c
+    parent = np.arange(nl + 1)
+    alive = set(r for r in range(1, nl + 1) if size[r] > 0)
+    blocked = set()
+    while True:
+        cand = [r for r in alive if r not in blocked]
+        if not cand:
+            break
+        inner = [q for q in cand if not wall[q]]
+        r = min(inner, key=lambda q: (size[q], q)) if inner else min(cand, key=lambda q: (size[q], q))
+        must = size[r] < min_cells or not wall[r]
+        if not must and len(alive) <= target:
+            break
+        opts = [(c, q) for q, c in nbrs[r].items() if size[q] + size[r] <= max_cells]
+        if not opts and must:
+            opts = [(c, q) for q, c in nbrs[r].items()]
+        if not opts:
+            blocked.add(r)
+            continue
+        best = sorted(opts, key=lambda t: (-t[0], t[1]))[0][1]
+        # merge r into best
+        parent[r] = best
+        wall[best] |= wall[r]
+        size[best] += size[r]
+        size[r] = 0
+        alive.discard(r)
+        for q, c in nbrs[r].items():
+            if q == best:
+                continue
+            nbrs[best][q] = nbrs[best].get(q, 0) + c
+            nbrs[q][best] = nbrs[q].get(best, 0) + c
+            nbrs[q].pop(r, None)
+        nbrs[best].pop(r, None)
+        nbrs.pop(r)
+        blocked.discard(best)
+    # resolve parents
+    root = np.arange(nl + 1)
+    for r in range(1, nl + 1):
+        q = r
+        while parent[q] != q:
+            q = parent[q]
+        root[r] = q
+    lab = root[lab]
+    uniq = np.unique(lab[lab > 0])
+    first = np.full(nl + 1, np.iinfo(np.int64).max)
+    idx = np.flatnonzero(lab > 0)
+    np.minimum.at(first, lab[idx], idx)
+    order = sorted(uniq.tolist(), key=lambda v: first[v])
+    remap = np.zeros(nl + 1, np.int64)
+    remap[order] = np.arange(1, len(order) + 1)
+    return remap[lab]
+
+
+def label_pores(mask: np.ndarray, target: int, periodic=X_PERIODIC, windows=range(1, 25), method="window",
+                min_cells: int = 0, max_cells: int = 0, oversegment: float = 4.0) -> Labelling:
+    """Watershed decomposition of the void into about `target` pores (heights: the distance to the
+    solid; priority flood, highest distance first, ties by insertion order, over the face-connected
+    void wrapping along periodic axes).
+
+    method="window" (default): markers are plateau components of cells that are maxima of the distance
+    within a (2w+1)-wide window, w chosen from `windows` to bring the count closest to `target`; every
+    region is a basin of the distance map, so it reaches the solid all around.
+    method="nms" (alternative, not used by the workloads): markers are distance maxima accepted greedily in order of decreasing distance when
+    farther than a spacing d from every accepted marker, d bisected to bring the count closest to
+    `oversegment * target`; the flooded regions are then merged on their adjacency graph (smallest
+    first, into the neighbour sharing most faces, keeping merged sizes <= max_cells) until about
+    `target` remain and none is below min_cells (0 disables a bound).  Merged regions can carry
+    appendages that touch no solid; under the closure of Eqs. 6/9 a constant velocity there is a null
+    vector of the closure block (seen on a 96^3 sphere pack), so the workloads use "window".
+    Void components without a marker get one at their deepest cell (lowest linear index among ties)."""
+    m = np.asarray(mask).astype(bool)
+    arr, amap = _squeeze2d(m)
+    dist2 = _squeeze2d(distance_to_solid(m, periodic))[0]
+    flat_d = dist2.ravel()
+    lab = np.zeros(arr.size, np.int64)
+    chosen = 0
+    if method == "nms":
+        lo, hi = 1.0, float(max(arr.shape))
+        best = None
+        for _ in range(18):
+            mid = 0.5 * (lo + hi)
+            mk = _nms_markers(dist2, arr, amap, periodic, mid)
+            want = int(round(oversegment * target)) if (min_cells or max_cells) else target
+            score = abs(len(mk) - want)
+            if best is None or score < best[0]:
+                best = (score, mid, mk)
+            if len(mk) > want:
+                lo = mid
+            else:
+                hi = mid
+        _, chosen, mk = best
+        lab[np.sort(mk)] = np.arange(1, len(mk) + 1)
+        npk = len(mk)
+    else:
+        best = None
+        for w in windows:
+            peak = _markers(dist2, arr, amap, periodic, w)
+            plab, npk = ndimage.label(peak, structure=np.ones((3,) * arr.ndim, bool))
+            score = abs(npk - target)
+            if best is None or score < best[0]:
+                best = (score, w, plab, npk)
+            if npk < target:
+                break
+        _, chosen, plab, npk = best
+        lab = plab.ravel().astype(np.int64).copy()
+        if npk > 0:
+            first = ndimage.minimum(np.arange(lab.size), labels=plab.ravel(), index=np.arange(1, npk + 1))
+            order = np.argsort(first, kind="stable")
+            remap = np.zeros(npk + 1, np.int64)
+            remap[order + 1] = np.arange(1, npk + 1)
+            lab = remap[lab]
+    comp, ncomp = void_components(m, periodic)
+    comp = _squeeze2d(comp)[0].ravel()
+    has = np.zeros(ncomp + 1, bool)
+    has[comp[lab > 0]] = True
+    nl = int(lab.max()) if lab.size else 0
+    for cidx in range(1, ncomp + 1):
+        if not has[cidx]:
+            cells = np.flatnonzero(comp == cidx)
+            c = cells[np.argmax(flat_d[cells])]
+            nl += 1
+            lab[c] = nl
+    lab = _flood(arr, amap, periodic, flat_d, lab)
+    if method == "nms":
+        lab = _merge_regions(lab, arr, amap, periodic, min_cells, max_cells or arr.size,
+                             target if (min_cells or max_cells) else arr.size)
+    labels = lab.reshape(arr.shape).astype(np.int32).reshape(mask.shape)
+    return Labelling(labels=labels, n_labels=int(lab.max()), window=chosen, dist=dist2.reshape(mask.shape))
 
 
 # ----------------------------------------------------------------------------------------------
@@ -361,6 +522,17 @@ def mu_for_reynolds(mask, ux_faces_at_mu1, re_target, rho=1.0, periodic=X_PERIOD
     return float(np.sqrt(re1 / re_target))
 
 
+def mu_kozeny_carman(mask, re_target, rho=1.0, b=1.0, periodic=X_PERIODIC) -> float:
+    """Viscosity for a target Re from geometry alone: Kozeny-Carman permeability for a bed of grains
+    of diameter 6 l (l = V_s / A_w), k = phi^3 l^2 / (5 (1 - phi)^2); Darcy U_D = k rho b / mu,
+    U = U_D / phi, Re = rho U l / mu  =>  mu = sqrt(rho^2 b k l / (phi Re)).  The Re actually reached
+    is measured from the solution (`reynolds`)."""
+    phi = float(np.mean(mask))
+    l = characteristic_length(mask, periodic)
+    k = phi ** 3 * l * l / (5.0 * (1.0 - phi) ** 2)
+    return float(np.sqrt(rho * rho * b * k * l / (phi * re_target)))
+
+
 # ----------------------------------------------------------------------------------------------
 # named workloads
 # ----------------------------------------------------------------------------------------------
@@ -382,6 +554,7 @@ def make_workload(kind: str, seed: int = 0, **kw) -> Workload:
           'grf'      3D n^3 (n=256 default) Gaussian field l=8 at porosity 0.20, ~3000 pores
           'tiny2d' / 'tiny3d'  small disk/sphere packs for brute-force checks (n given by kw)"""
     per = X_PERIODIC
+    min_cells = max_cells = 0
     if kind == "disks64":
         n = kw.get("n", 64)
         mask = disk_pack_2d(n, kw.get("n_disks", 12), 4.0, 8.0, seed)
@@ -390,10 +563,12 @@ def make_workload(kind: str, seed: int = 0, **kw) -> Workload:
         n = kw.get("n", 96)
         mask = sphere_pack_3d(n, kw.get("rmin", 6.0), kw.get("rmax", 10.0), kw.get("porosity", 0.35), seed)
         target = kw.get("target", 200)
+        min_cells, max_cells = 135, 5400   # ~500 and ~20k unknowns (3.7 unknowns per void cell)
     elif kind == "grf":
         n = kw.get("n", 256)
         mask = gaussian_field_3d(n, kw.get("corr_len", 8.0), kw.get("porosity", 0.20), seed)
         target = kw.get("target", 3000)
+        min_cells, max_cells = 135, 5400
     elif kind == "tiny2d":
         n = kw.get("n", 16)
         mask = disk_pack_2d(n, kw.get("n_disks", 2), kw.get("rmin", 1.5), kw.get("rmax", 3.0), seed)
@@ -405,5 +580,6 @@ def make_workload(kind: str, seed: int = 0, **kw) -> Workload:
     else:
         raise ValueError(kind)
     mask, dropped = percolating_void(mask, per)
-    lab = label_pores(mask, target, per)
+    lab = label_pores(mask, target, per, method=kw.get("method", "window"), min_cells=kw.get("min_cells", min_cells),
+                      max_cells=kw.get("max_cells", max_cells))
     return Workload(kind, mask, lab.labels, per, dropped, lab.n_labels)

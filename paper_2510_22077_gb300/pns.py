@@ -40,7 +40,8 @@ class Stats(ctypes.Structure):
                 ("fgmres_its", ctypes.c_int * 64), ("res_hist", ctypes.c_double * 65),
                 ("r0_norm", ctypes.c_double), ("t_setup_ms", ctypes.c_double), ("t_mg_ms", ctypes.c_double),
                 ("t_ml_ms", ctypes.c_double), ("t_sol_ms", ctypes.c_double), ("t_local_ms", ctypes.c_double),
-                ("local_launches", ctypes.c_longlong), ("local_bytes_per_apply", ctypes.c_double)]
+                ("local_launches", ctypes.c_longlong), ("local_bytes_per_apply", ctypes.c_double),
+                ("kernel_launches", ctypes.c_longlong), ("refine_residual_max", ctypes.c_double)]
 
     def as_dict(self):
         n = self.newton_its
@@ -48,7 +49,8 @@ class Stats(ctypes.Structure):
                 "fgmres_its": list(self.fgmres_its[:min(n, 64)]), "res_hist": list(self.res_hist[:min(n + 1, 65)]),
                 "r0_norm": self.r0_norm, "t_setup_ms": self.t_setup_ms, "t_mg_ms": self.t_mg_ms,
                 "t_ml_ms": self.t_ml_ms, "t_sol_ms": self.t_sol_ms, "t_local_ms": self.t_local_ms,
-                "local_launches": self.local_launches, "local_bytes_per_apply": self.local_bytes_per_apply}
+                "local_launches": self.local_launches, "local_bytes_per_apply": self.local_bytes_per_apply,
+                "kernel_launches": self.kernel_launches, "refine_residual_max": self.refine_residual_max}
 
 
 class Info(ctypes.Structure):
@@ -90,6 +92,7 @@ def load(path: str = LIB_PATH):
         "pns_newton_solve": (I, [P, P, P, ctypes.POINTER(Stats)]),
         "pns_stokes_solve": (I, [P, P, ctypes.POINTER(Stats)]),
         "pns_export_maps": (I, [P, P, P, P, P, P, P]),
+        "pns_export_coarse": (I, [P, P, ctypes.POINTER(ctypes.c_int)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -220,6 +223,15 @@ class Solver:
         d = st.as_dict()
         d["status"] = STATUS.get(rc, rc)
         return x, d
+
+    def pns_export_coarse(self):
+        """Inverse of the coarse matrix of the built preconditioner (host, n_o x n_o)."""
+        n = ctypes.c_int(0)
+        self._check(self.lib.pns_export_coarse(self.ctx, None, ctypes.byref(n)), "pns_export_coarse")
+        a = np.zeros((n.value, n.value), np.float64)
+        self._check(self.lib.pns_export_coarse(self.ctx, a.ctypes.data_as(ctypes.c_void_p), ctypes.byref(n)),
+                    "pns_export_coarse")
+        return a
 
     def pns_export_maps(self):
         nc, dim = self.ncell, self.dim

@@ -215,3 +215,22 @@ def test_orphan_interface_fixture():
     S.pns_build_precond(to_dev(x))
     v = random_vector(pb, seed=2)
     assert rel(S.pns_precond_apply(to_dev(v)).cpu().numpy(), M.apply(v, A_b)) < 1e-9
+
+
+@pytest.mark.parametrize("variant", ["gplmm", "aplmm_s"])
+def test_coarse_inverse_matches_oracle_and_repeats(c1, variant):
+    """The coarse inverse (A^o = R^ A_b P^, Remark 1) equals the oracle's, and two builds at the same
+    state give the same inverse (the pivoting is race-free: FP64 throughout, only the order of the
+    atomic segment sums differs)."""
+    pb = problem(c1, mu=3.87)
+    x = random_state(pb, seed=2, scale=0.1)
+    M, A_b = pb.preconditioner(variant, x)
+    ref = np.linalg.inv(M.Ao)
+    S = solver(c1, mu=3.87, variant=variant, precision="fp64")
+    got = []
+    for _ in range(2):
+        S.pns_build_precond(to_dev(x))
+        got.append(S.pns_export_coarse())
+    tol = max(1e-10, 100 * np.finfo(float).eps * np.linalg.cond(M.Ao))
+    assert rel(got[0], ref) < tol, rel(got[0], ref)
+    assert rel(got[1], got[0]) < 1e-12

@@ -75,7 +75,9 @@ def test_coarse_is_projection_and_consistent(variant):
     v = np.zeros(g.nfull)
     v[unk] = rng.standard_normal(len(unk))
     res = M.Rhat @ (v - A_b @ M.coarse(v))
-    assert np.abs(res).max() <= 1e-12 * np.abs(M.Rhat @ v).max()
+    # exact in exact arithmetic; the coarse LU solve leaves cond(A^o) * eps
+    tol = max(1e-12, 100 * np.finfo(float).eps * np.linalg.cond(M.Ao))
+    assert np.abs(res).max() <= tol * np.abs(M.Rhat @ v).max()
 
 
 def test_correction_vector_scale_invariance():
