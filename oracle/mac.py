@@ -2,7 +2,7 @@
 
 Follows Eq. 1 (governing equations), Eq. 3 (Newton system J dx = -r with J = [[F, G^T], [G, O]])
 and Sec. 2 (MAC: velocity on cell faces, pressure at cell centres, grid = image voxels).
-The details the paper leaves open are fixed as follows (the readings are listed in the design doc):
+The details the paper leaves open are fixed as follows:
 
 * h = 1.  Periodic along axes flagged in `periodic` (default x only); other box faces are no-slip
   walls; void-solid faces are no-slip.

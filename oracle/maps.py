@@ -1,6 +1,6 @@
 """Domain decomposition index maps (Sec. 3.2.1 and the permutation paragraph of Sec. 3.2.2; Sec. 4).
 
-Readings fixed where the paper is silent (listed in the design doc):
+Readings fixed where the paper is silent:
 
 * Contact interfaces (Sec. 3.2.2, "thinnest 4-/6-connected collection of pixels that separate two
   primary grids", one interface Gamma_ij per pair of adjacent primary grids): a void cell of label a

@@ -21,7 +21,7 @@ Two independent formulations are given:
   Eqs. 6 and 9, Q of Eq. 11, P of Eq. 14, R of Eq. 18 and E/R of Eq. 25 as explicit matrices,
   multiplied out densely.
 
-Readings (DESIGN.md): f faces get zero in P^ (no Eq. 8 back-substitution); interfaces adjacent to no
+Readings: f faces get zero in P^ (no Eq. 8 back-substitution); interfaces adjacent to no
 primary grid get no coarse unknown (their cells get zero in P^ and no row of R^); Pi(C^T) is the structural
 pattern of C (every unknown of p_i); b_B = -r(u=0, p=0) with the previous time level zero, i.e. rho b
 on face rows and 0 on cell rows; the coarse unknowns are ordered [x^o (coarse interfaces); y^o (primary)].
