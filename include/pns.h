@@ -161,6 +161,17 @@ int pns_build_precond(pns_ctx* ctx, const double* x_lin);
  * PNS_ERR_STATE before pns_build_precond. */
 int pns_precond_apply(pns_ctx* ctx, const double* v, double* z);
 
+/* z = M^{-1} v exactly as pns_precond_apply, but without allocating device memory during the call:
+ * for callers that cannot call cudaMalloc when they apply the preconditioner (a device allocator
+ * owned by someone else, or a footprint that must stay fixed after start-up).  The scratch vectors
+ * live in one file-scope device array of 24 MiB, enough for a full layout of about 500,000 entries;
+ * larger problems return PNS_ERR_ARG with a message.  The array is shared by every call in the
+ * process, so calls that overlap on the GPU race on it.  Its device address is looked up once per
+ * device on the first call with that device current: make that first call before any stream capture.
+ * Every GPU that loads the library holds the array until exit.  The paper has no counterpart: this is
+ * an interface of this library.  PNS_ERR_STATE before pns_build_precond. */
+int pns_precond_apply_static(pns_ctx* ctx, const double* v, double* z);
+
 /* Newton-FGMRES (Sec. 8).  x: device, full layout; initial guess on input, solution on output.
  * x_prev: previous time level (transient) or NULL.  Builds the preconditioner at the initial
  * guess if none is built.  st may be NULL.  Synchronises.  PNS_ERR_NOT_CONVERGED if max_newton is

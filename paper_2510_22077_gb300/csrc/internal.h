@@ -183,3 +183,8 @@ cudaError_t launch_trisolve_update(const double* H, int ldh, const double* g, in
                                    long long ld, double* x, long long n, cudaStream_t s);
 
 }  // namespace pns
+
+// The opaque handle of the C ABI.
+struct pns_ctx {
+  pns::Ctx c;
+};

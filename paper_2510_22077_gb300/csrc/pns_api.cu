@@ -13,10 +13,6 @@
 
 using namespace pns;
 
-struct pns_ctx {
-  Ctx c;
-};
-
 #include <atomic>
 namespace pns {
 static std::atomic<long long> g_launches{0};

@@ -89,6 +89,7 @@ def load(path: str = LIB_PATH):
         "pns_operator_apply": (I, [P, I, P, P, P]),
         "pns_build_precond": (I, [P, P]),
         "pns_precond_apply": (I, [P, P, P]),
+        "pns_precond_apply_static": (I, [P, P, P]),
         "pns_newton_solve": (I, [P, P, P, ctypes.POINTER(Stats)]),
         "pns_stokes_solve": (I, [P, P, ctypes.POINTER(Stats)]),
         "pns_export_maps": (I, [P, P, P, P, P, P, P]),
@@ -203,6 +204,12 @@ class Solver:
     def pns_precond_apply(self, v, z=None):
         z = self.zeros() if z is None else z
         self._check(self.lib.pns_precond_apply(self.ctx, _ptr(v), _ptr(z)), "pns_precond_apply")
+        return z
+
+    def pns_precond_apply_static(self, v, z=None):
+        """z = M^{-1} v with no device allocation inside the call (scratch in a fixed device array)."""
+        z = self.zeros() if z is None else z
+        self._check(self.lib.pns_precond_apply_static(self.ctx, _ptr(v), _ptr(z)), "pns_precond_apply_static")
         return z
 
     def pns_newton_solve(self, x, x_prev=None, check=True):
