@@ -185,7 +185,9 @@ int pns_stokes_solve(pns_ctx* ctx, double* x, pns_stats* st);
 
 /* Copy the inverse of the coarse matrix A^o = R^ A_b P^ (Remark 1) of the built preconditioner to a
  * HOST array of n_o * n_o doubles (row-major); *n_o receives the coarse size (coarse interfaces
- * first, then primary grids).  ao_inv may be NULL to query n_o.  PNS_ERR_STATE before a build or
+ * first, then primary grids).  A primary grid on which rho b vanishes (no face unknown along a
+ * nonzero component of b) has a zero correction vector and no coarse unknown: its row and column
+ * are those of the identity.  ao_inv may be NULL to query n_o.  PNS_ERR_STATE before a build or
  * for ML_ONLY.  Synchronises. */
 int pns_export_coarse(const pns_ctx* ctx, double* ao_inv, int* n_o);
 

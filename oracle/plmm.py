@@ -22,7 +22,9 @@ Two independent formulations are given:
   multiplied out densely.
 
 Readings: f faces get zero in P^ (no Eq. 8 back-substitution); interfaces adjacent to no
-primary grid get no coarse unknown (their cells get zero in P^ and no row of R^); Pi(C^T) is the structural
+primary grid get no coarse unknown (their cells get zero in P^ and no row of R^); a primary grid on which
+b_B vanishes (no face unknown along the body force) gets no coarse unknown either: its correction vector
+c^{p_i} = 0 would be a zero column of P^ and leave A^o singular; Pi(C^T) is the structural
 pattern of C (every unknown of p_i); b_B = -r(u=0, p=0) with the previous time level zero, i.e. rho b
 on face rows and 0 on cell rows; the coarse unknowns are ordered [x^o (coarse interfaces); y^o (primary)].
 """
@@ -65,12 +67,17 @@ class Plmm:
         self.g, self.m = g, m
         self.use_coarse = use_coarse
         self.n_ci = len(m.coarse_ifaces)
-        self.n_o = self.n_ci + m.n_prim
+        bB = source_rhs(g, prm)
+        # primary grids with a coarse unknown y^o_i: those whose correction vector is not zero
+        self.coarse_prim = np.array([i for i in range(m.n_prim) if np.any(bB[m.prim_unknowns[i]] != 0.0)],
+                                    np.int64)
+        self.coarse_of_prim = np.full(m.n_prim, -1, np.int64)
+        self.coarse_of_prim[self.coarse_prim] = self.n_ci + np.arange(len(self.coarse_prim))
+        self.n_o = self.n_ci + len(self.coarse_prim)
         self.lu_p = [spla.splu(A_b[P][:, P].tocsc()) for P in m.prim_unknowns]
         self.lu_d = [spla.splu(A_b[D][:, D].tocsc()) for D in m.dual_unknowns]
         if not use_coarse:
             return
-        bB = source_rhs(g, prm)
         # prolongation P^ (nfull x n_o): shape vectors, correction vectors, 1 on interface cells
         prow, pcol, pval = [], [], []
         self.shape = []
@@ -91,9 +98,10 @@ class Plmm:
             c = lu_bar.solve(bB[Pi])
             self.shape.append(sh)
             self.corr.append(c)
-            prow.append(Pi)
-            pcol.append(np.full(len(Pi), self.n_ci + i))
-            pval.append(c)
+            if self.coarse_of_prim[i] >= 0:
+                prow.append(Pi)
+                pcol.append(np.full(len(Pi), self.coarse_of_prim[i]))
+                pval.append(c)
         for k, j in enumerate(m.coarse_ifaces):
             cells = g.pidx(m.iface_cells[j])
             prow.append(cells)
@@ -107,9 +115,9 @@ class Plmm:
             cells = g.pidx(m.iface_cells[j])
             rrow.append(np.full(len(cells), k))
             rcol.append(cells)
-        for i in range(m.n_prim):
+        for i in self.coarse_prim:
             Pi = m.prim_unknowns[i]
-            rrow.append(np.full(len(Pi), self.n_ci + i))
+            rrow.append(np.full(len(Pi), self.coarse_of_prim[i]))
             rcol.append(Pi)
         rr = np.concatenate(rrow)
         self.Rhat = sp.csr_matrix((np.ones(len(rr)), (rr, np.concatenate(rcol))), shape=(self.n_o, g.nfull))
@@ -204,16 +212,18 @@ def literal_preconditioner(g, prm, m, A_b, A_solve, use_coarse=True):
     # Eq. 17: C = blockdiag(c^{p_i}),  c^{p_i} = (Abar^{p_i})^{-1} b_B^{p_i}
     bB_full = source_rhs(g, prm)[unk]
     bB_p = (W.T @ bB_full)[:Np]
-    Cm = np.zeros((Np, m.n_prim))
-    for i in range(m.n_prim):
+    # a primary grid whose b_B is zero has c^{p_i} = 0: its column of C and row of Pi(C^T) are left out
+    kept = [i for i in range(m.n_prim) if np.any(bB_p[bounds[i]:bounds[i + 1]] != 0.0)]
+    Cm = np.zeros((Np, len(kept)))
+    for k, i in enumerate(kept):
         si = slice(bounds[i], bounds[i + 1])
-        Cm[si, i] = np.linalg.solve(Abar_pp_M[si, si], bB_p[si])
-    Pm = np.block([[B, Cm], [np.eye(nci), np.zeros((nci, m.n_prim))]])   # Eq. 14
+        Cm[si, k] = np.linalg.solve(Abar_pp_M[si, si], bB_p[si])
+    Pm = np.block([[B, Cm], [np.eye(nci), np.zeros((nci, len(kept)))]])   # Eq. 14
     # Eq. 18 with the structural pattern of C
-    PiCT = np.zeros((m.n_prim, Np))
-    for i in range(m.n_prim):
-        PiCT[i, bounds[i]:bounds[i + 1]] = 1.0
-    Rm = np.block([[np.zeros((nci, Np)), np.eye(nci)], [PiCT, np.zeros((m.n_prim, nci))]])
+    PiCT = np.zeros((len(kept), Np))
+    for k, i in enumerate(kept):
+        PiCT[k, bounds[i]:bounds[i + 1]] = 1.0
+    Rm = np.block([[np.zeros((nci, Np)), np.eye(nci)], [PiCT, np.zeros((len(kept), nci))]])
     # Eq. 21: P^ = W Q P (f rows zero), R^ = R Q^T W^T (f columns dropped)
     QP = Q @ Pm
     QP_full = np.vstack([QP, np.zeros((N - Np - Nc, QP.shape[1]))])

@@ -160,6 +160,10 @@ __global__ void k_setcol(double* __restrict__ A, int n, int k, const double* __r
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) A[(long long)i * n + k] = col[i];
 }
+__global__ void k_unitrow(double* __restrict__ A, int n, int k) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < n) A[(long long)k * n + j] = (j == k) ? 1.0 : 0.0;
+}
 
 // local inverses of one block set in the storage type of `precision`
 int to_bf16(Ctx& C, BlockSet& B) {
@@ -295,6 +299,17 @@ int build_coarse_t(Ctx& C, Precond& pc, int* d_bad) {
   CK(cudaMemcpyAsync(pc.basis.p, out.p, sizeof(double) * rtot, cudaMemcpyDeviceToDevice, s));
   // coarse matrix A^o = R^ A_b P^ column by column (prolong e_k, apply A_b, restrict)
   const int no = pc.n_o;
+  // A primary grid on which b_B = rho b vanishes (no face unknown along a nonzero component of b) has
+  // a zero correction vector, hence a zero column of P^ and of A^o.  It has no coarse unknown: its row
+  // and column of A^o are replaced by those of the identity, which leaves the solution of the other
+  // coarse unknowns unchanged and multiplies the zero vector in the prolongation.
+  std::vector<char> no_source(M.n_prim, 1);
+  for (int i = 0; i < M.n_prim; ++i)
+    for (int u : M.prim_unk[i])
+      if (u < C.G.dim * C.G.ncell && C.P.rho * C.P.b[u / C.G.ncell] != 0.0) {
+        no_source[i] = 0;
+        break;
+      }
   DevBuf Ao, ek, zf, yf, col, work, perm;
   CK(dalloc(Ao, sizeof(double) * (size_t)no * no));
   CK(dalloc(ek, sizeof(double) * no));
@@ -302,6 +317,12 @@ int build_coarse_t(Ctx& C, Precond& pc, int* d_bad) {
   CK(dalloc(yf, sizeof(double) * C.nfull));
   CK(dalloc(col, sizeof(double) * no));
   for (int k = 0; k < no; ++k) {
+    if (k >= pc.n_cif && no_source[k - pc.n_cif]) {
+      { pns::count_launch(); k_unit<<<(no + 255) / 256, 256, 0, s>>>(col.as<double>(), no, k); }
+      { pns::count_launch(); k_setcol<<<(no + 255) / 256, 256, 0, s>>>(Ao.as<double>(), no, k, col.as<double>()); }
+      CK(cudaGetLastError());
+      continue;
+    }
     { pns::count_launch(); k_unit<<<(no + 255) / 256, 256, 0, s>>>(ek.as<double>(), no, k); }
     CK((launch_prolong<double, double>(C, pc, ek.as<double>(), zf.as<double>())));
     CK(launch_apply<double>(C, pc.op, pc.state.as<double>(), zf.as<double>(), nullptr, yf.as<double>(), true));
@@ -309,6 +330,9 @@ int build_coarse_t(Ctx& C, Precond& pc, int* d_bad) {
     { pns::count_launch(); k_setcol<<<(no + 255) / 256, 256, 0, s>>>(Ao.as<double>(), no, k, col.as<double>()); }
     CK(cudaGetLastError());
   }
+  for (int i = 0; i < M.n_prim; ++i)
+    if (no_source[i]) { pns::count_launch(); k_unitrow<<<(no + 255) / 256, 256, 0, s>>>(Ao.as<double>(), no, pc.n_cif + i); }
+  CK(cudaGetLastError());
   CK(dalloc(work, sizeof(double) * no));
   CK(dalloc(perm, sizeof(int) * no));
   CK(launch_coarse_invert(Ao.as<double>(), no, work.as<double>(), perm.as<int>(), d_bad, s));

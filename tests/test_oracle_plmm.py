@@ -223,3 +223,34 @@ def test_orphan_interface_gets_no_coarse_unknown():
         zl = Mlit @ v[unk]
         assert np.linalg.norm(M.apply(v, A_b)[unk] - zl) / np.linalg.norm(zl) < 1e-11
         assert M.coarse(v)[pb.g.pidx(7)] == 0.0
+
+
+def test_primary_grid_without_source_gets_no_coarse_unknown():
+    """6 x 5, x-periodic, body force along x.  A channel of label 1 (rows 0-2) with a one-cell-wide
+    dead-end branch of label 2 (column 2, rows 3-5).  The branch's primary grid holds three cells and
+    three y faces and no x face, so b_B = rho b vanishes on it and its correction vector
+    c = Abar^{-1} b_B is zero: a coarse unknown for it would be a zero column of P^ and make A^o
+    singular.  It must get none; the literal and recipe forms still agree."""
+    lab = np.zeros((6, 5), int)
+    lab[0:3, :] = 1
+    lab[3:6, 2] = 2
+    mask = (lab > 0).astype(np.uint8)[None]
+    pb = krylov.Problem(mask, lab[None].astype(np.int32), mac.Params(1.0, 0.5, (1.0, 0.0)))
+    g, m = pb.g, pb.maps
+    # hand-derived: interface = channel cell (row 2, col 2) = 12; the branch primary grid holds the
+    # y faces of cells 17, 22, 27 (rows 3-5 of column 2) and their three cells
+    assert [sorted(c.tolist()) for c in m.iface_cells] == [[12]]
+    assert sorted(m.prim_unknowns[1].tolist()) == [g.fidx(1, 17), g.fidx(1, 22), g.fidx(1, 27),
+                                                   g.pidx(17), g.pidx(22), g.pidx(27)]
+    assert [list(c) for c in m.C] == [[0], [0]]
+    x = krylov.stokes_solution(pb)
+    for variant in ["gplmm", "aplmm_s"]:
+        M, A_b = pb.preconditioner(variant, x)
+        assert list(M.coarse_prim) == [0] and list(M.coarse_of_prim) == [1, -1] and M.n_o == 2
+        assert not np.any(M.corr[1])
+        assert np.linalg.cond(M.Ao) < 1e12
+        Mlit, _, unk = plmm.literal_preconditioner(pb.g, pb.prm, m, A_b, A_b)
+        v = np.zeros(pb.g.nfull)
+        v[unk] = np.random.default_rng(0).standard_normal(len(unk))
+        zl = Mlit @ v[unk]
+        assert np.linalg.norm(M.apply(v, A_b)[unk] - zl) / np.linalg.norm(zl) < 1e-11
