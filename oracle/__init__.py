@@ -11,6 +11,7 @@ Modules
     maps    -- primary grids, contact interfaces, face classes, dual grids, gPLMM tags  (Sec. 3.2.1, 4)
     plmm    -- preconditioner build and apply, recipe form and literal matrix form  (Eqs. 5-26)
     krylov  -- right-preconditioned flexible GMRES, Newton, backward-Euler stepping  (Sec. 8, Eq. 3)
+    block   -- block-triangular Schur comparator with the scaled BFBt approximation  (Sec. 1, Eq. 4)
 
 Parity status: every function is pinned by a test in tests/test_oracle_*.py against something
 other than itself (closed forms, finite differences, brute-force dense solves, the projection
