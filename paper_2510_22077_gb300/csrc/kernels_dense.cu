@@ -10,6 +10,7 @@
 
 #include <algorithm>
 #include <cstring>
+#include <type_traits>
 #include <vector>
 
 #include "internal.h"
@@ -90,20 +91,23 @@ __global__ void k_assemble(Geo G, Phy P, const uint8_t* __restrict__ fl, int op,
 }
 
 // ------------------------------------------------------------------------------ Gauss-Jordan
-// step k: panel rows/cols [k*TB, k*TB + nb).  Active blocks are the first `cnt` of `order`.
-template <typename ST>
+// Blocked Gauss-Jordan with panel width TBK (64 for FP64, 128 for FP32).  Step k: panel rows/cols
+// [k*TBK, k*TBK + nb).  Active blocks are the first `cnt` of `order`.  256 threads per CTA; the panel
+// kernels give each thread an R x R patch (R = TBK / 16).
+template <typename ST, int TBK>
 __global__ void k_gj_diag(int k, const int* __restrict__ order, const int* __restrict__ bn,
                           const int* __restrict__ bld, const long long* __restrict__ moff, ST* __restrict__ mat,
                           int* __restrict__ bad) {
-  __shared__ ST D[TB][TB + 1];
-  __shared__ ST colt[TB];
+  extern __shared__ unsigned char smraw[];
+  ST(*D)[TBK + 1] = (ST(*)[TBK + 1])smraw;
+  ST* colt = (ST*)(smraw + sizeof(ST) * TBK * (TBK + 1));
   int b = order[blockIdx.x];
   int n = bn[b], ld = bld[b];
-  int p0 = k * TB;
-  int nb = min(TB, n - p0);
+  int p0 = k * TBK;
+  int nb = min(TBK, n - p0);
   ST* A = mat + moff[b] + (long long)p0 * ld + p0;
-  for (int e = threadIdx.x; e < TB * TB; e += blockDim.x) {
-    int i = e / TB, j = e % TB;
+  for (int e = threadIdx.x; e < TBK * TBK; e += blockDim.x) {
+    int i = e / TBK, j = e % TBK;
     D[i][j] = (i < nb && j < nb) ? A[(long long)i * ld + j] : (ST)0;
   }
   __syncthreads();
@@ -140,80 +144,94 @@ __global__ void k_gj_diag(int k, const int* __restrict__ order, const int* __res
 __device__ __forceinline__ int tile_skip(int t, int k) { return t + (t >= k); }
 
 // A[P, J] <- Dinv * A[P, J] for every column tile J != k
-template <typename ST>
+template <typename ST, int TBK>
 __global__ void k_gj_rowpanel(int k, int cnt, const int* __restrict__ order, const long long* __restrict__ pre1,
                               const int* __restrict__ bn, const int* __restrict__ bld,
                               const long long* __restrict__ moff, ST* __restrict__ mat) {
+  constexpr int R = TBK / 16;
   extern __shared__ unsigned char smraw[];
-  ST(*Dv)[TB + 1] = (ST(*)[TB + 1])smraw;
-  ST(*Tl)[TB + 1] = (ST(*)[TB + 1])(smraw + sizeof(ST) * TB * (TB + 1));
+  ST(*Dv)[TBK + 1] = (ST(*)[TBK + 1])smraw;
+  ST(*Tl)[TBK + 1] = (ST(*)[TBK + 1])(smraw + sizeof(ST) * TBK * (TBK + 1));
   long long w = blockIdx.x;
   int s = find_block(pre1, cnt, w);
   int b = order[s];
   int jt = tile_skip((int)(w - pre1[s]), k);
   int n = bn[b], ld = bld[b];
-  int p0 = k * TB, j0 = jt * TB;
-  int nb = min(TB, n - p0), nj = min(TB, n - j0);
+  int p0 = k * TBK, j0 = jt * TBK;
+  int nb = min(TBK, n - p0), nj = min(TBK, n - j0);
   ST* A = mat + moff[b];
-  for (int e = threadIdx.x; e < TB * TB; e += blockDim.x) {
-    int i = e / TB, j = e % TB;
+  for (int e = threadIdx.x; e < TBK * TBK; e += blockDim.x) {
+    int i = e / TBK, j = e % TBK;
     Dv[i][j] = (i < nb && j < nb) ? A[(long long)(p0 + i) * ld + p0 + j] : (ST)0;
     Tl[i][j] = (i < nb && j < nj) ? A[(long long)(p0 + i) * ld + j0 + j] : (ST)0;
   }
   __syncthreads();
   int ty = threadIdx.x / 16, tx = threadIdx.x % 16;
-  ST acc[4][4] = {};
+  ST acc[R][R] = {};
   for (int kk = 0; kk < nb; ++kk) {
-    ST a[4], bb[4];
-    for (int i = 0; i < 4; ++i) a[i] = Dv[ty * 4 + i][kk];
-    for (int j = 0; j < 4; ++j) bb[j] = Tl[kk][tx * 4 + j];
-    for (int i = 0; i < 4; ++i)
-      for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * bb[j];
+    ST a[R], bb[R];
+#pragma unroll
+    for (int i = 0; i < R; ++i) a[i] = Dv[ty * R + i][kk];
+#pragma unroll
+    for (int j = 0; j < R; ++j) bb[j] = Tl[kk][tx * R + j];
+#pragma unroll
+    for (int i = 0; i < R; ++i)
+#pragma unroll
+      for (int j = 0; j < R; ++j) acc[i][j] += a[i] * bb[j];
   }
   __syncthreads();
-  for (int i = 0; i < 4; ++i)
-    for (int j = 0; j < 4; ++j) {
-      int r = ty * 4 + i, cc = tx * 4 + j;
+#pragma unroll
+  for (int i = 0; i < R; ++i)
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+      int r = ty * R + i, cc = tx * R + j;
       if (r < nb && cc < nj) A[(long long)(p0 + r) * ld + j0 + cc] = acc[i][j];
     }
 }
 
-// A[I, J] -= A[I, P] * A[P, J] for tiles I != k, J != k
-template <typename ST>
+// A[I, J] -= A[I, P] * A[P, J] for tiles I != k, J != k (FP64 path; FP32 uses k_mm128_gj_update)
+template <typename ST, int TBK>
 __global__ void k_gj_update(int k, int cnt, const int* __restrict__ order, const long long* __restrict__ pre2,
                             const int* __restrict__ bn, const int* __restrict__ bld, const long long* __restrict__ moff,
                             ST* __restrict__ mat) {
+  constexpr int R = TBK / 16;
   extern __shared__ unsigned char smraw[];
-  ST(*As)[TB + 1] = (ST(*)[TB + 1])smraw;
-  ST(*Bs)[TB + 1] = (ST(*)[TB + 1])(smraw + sizeof(ST) * TB * (TB + 1));
+  ST(*As)[TBK + 1] = (ST(*)[TBK + 1])smraw;
+  ST(*Bs)[TBK + 1] = (ST(*)[TBK + 1])(smraw + sizeof(ST) * TBK * (TBK + 1));
   long long w = blockIdx.x;
   int s = find_block(pre2, cnt, w);
   int b = order[s];
   int n = bn[b], ld = bld[b];
-  int T = (n + TB - 1) / TB;
+  int T = (n + TBK - 1) / TBK;
   long long loc = w - pre2[s];
   int it = tile_skip((int)(loc / (T - 1)), k), jt = tile_skip((int)(loc % (T - 1)), k);
-  int p0 = k * TB, i0 = it * TB, j0 = jt * TB;
-  int nb = min(TB, n - p0), ni = min(TB, n - i0), nj = min(TB, n - j0);
+  int p0 = k * TBK, i0 = it * TBK, j0 = jt * TBK;
+  int nb = min(TBK, n - p0), ni = min(TBK, n - i0), nj = min(TBK, n - j0);
   ST* A = mat + moff[b];
-  for (int e = threadIdx.x; e < TB * TB; e += blockDim.x) {
-    int i = e / TB, j = e % TB;
+  for (int e = threadIdx.x; e < TBK * TBK; e += blockDim.x) {
+    int i = e / TBK, j = e % TBK;
     As[i][j] = (i < ni && j < nb) ? A[(long long)(i0 + i) * ld + p0 + j] : (ST)0;
     Bs[i][j] = (i < nb && j < nj) ? A[(long long)(p0 + i) * ld + j0 + j] : (ST)0;
   }
   __syncthreads();
   int ty = threadIdx.x / 16, tx = threadIdx.x % 16;
-  ST acc[4][4] = {};
+  ST acc[R][R] = {};
   for (int kk = 0; kk < nb; ++kk) {
-    ST a[4], bb[4];
-    for (int i = 0; i < 4; ++i) a[i] = As[ty * 4 + i][kk];
-    for (int j = 0; j < 4; ++j) bb[j] = Bs[kk][tx * 4 + j];
-    for (int i = 0; i < 4; ++i)
-      for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * bb[j];
+    ST a[R], bb[R];
+#pragma unroll
+    for (int i = 0; i < R; ++i) a[i] = As[ty * R + i][kk];
+#pragma unroll
+    for (int j = 0; j < R; ++j) bb[j] = Bs[kk][tx * R + j];
+#pragma unroll
+    for (int i = 0; i < R; ++i)
+#pragma unroll
+      for (int j = 0; j < R; ++j) acc[i][j] += a[i] * bb[j];
   }
-  for (int i = 0; i < 4; ++i)
-    for (int j = 0; j < 4; ++j) {
-      int r = ty * 4 + i, cc = tx * 4 + j;
+#pragma unroll
+  for (int i = 0; i < R; ++i)
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+      int r = ty * R + i, cc = tx * R + j;
       if (r < ni && cc < nj) {
         ST* q = A + (long long)(i0 + r) * ld + j0 + cc;
         *q = *q - acc[i][j];
@@ -222,42 +240,235 @@ __global__ void k_gj_update(int k, int cnt, const int* __restrict__ order, const
 }
 
 // A[I, P] <- -A[I, P] * Dinv for row tiles I != k
-template <typename ST>
+template <typename ST, int TBK>
 __global__ void k_gj_colpanel(int k, int cnt, const int* __restrict__ order, const long long* __restrict__ pre1,
                               const int* __restrict__ bn, const int* __restrict__ bld,
                               const long long* __restrict__ moff, ST* __restrict__ mat) {
+  constexpr int R = TBK / 16;
   extern __shared__ unsigned char smraw[];
-  ST(*Dv)[TB + 1] = (ST(*)[TB + 1])smraw;
-  ST(*Tl)[TB + 1] = (ST(*)[TB + 1])(smraw + sizeof(ST) * TB * (TB + 1));
+  ST(*Dv)[TBK + 1] = (ST(*)[TBK + 1])smraw;
+  ST(*Tl)[TBK + 1] = (ST(*)[TBK + 1])(smraw + sizeof(ST) * TBK * (TBK + 1));
   long long w = blockIdx.x;
   int s = find_block(pre1, cnt, w);
   int b = order[s];
   int it = tile_skip((int)(w - pre1[s]), k);
   int n = bn[b], ld = bld[b];
-  int p0 = k * TB, i0 = it * TB;
-  int nb = min(TB, n - p0), ni = min(TB, n - i0);
+  int p0 = k * TBK, i0 = it * TBK;
+  int nb = min(TBK, n - p0), ni = min(TBK, n - i0);
   ST* A = mat + moff[b];
-  for (int e = threadIdx.x; e < TB * TB; e += blockDim.x) {
-    int i = e / TB, j = e % TB;
+  for (int e = threadIdx.x; e < TBK * TBK; e += blockDim.x) {
+    int i = e / TBK, j = e % TBK;
     Dv[i][j] = (i < nb && j < nb) ? A[(long long)(p0 + i) * ld + p0 + j] : (ST)0;
     Tl[i][j] = (i < ni && j < nb) ? A[(long long)(i0 + i) * ld + p0 + j] : (ST)0;
   }
   __syncthreads();
   int ty = threadIdx.x / 16, tx = threadIdx.x % 16;
-  ST acc[4][4] = {};
+  ST acc[R][R] = {};
   for (int kk = 0; kk < nb; ++kk) {
-    ST a[4], bb[4];
-    for (int i = 0; i < 4; ++i) a[i] = Tl[ty * 4 + i][kk];
-    for (int j = 0; j < 4; ++j) bb[j] = Dv[kk][tx * 4 + j];
-    for (int i = 0; i < 4; ++i)
-      for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * bb[j];
+    ST a[R], bb[R];
+#pragma unroll
+    for (int i = 0; i < R; ++i) a[i] = Tl[ty * R + i][kk];
+#pragma unroll
+    for (int j = 0; j < R; ++j) bb[j] = Dv[kk][tx * R + j];
+#pragma unroll
+    for (int i = 0; i < R; ++i)
+#pragma unroll
+      for (int j = 0; j < R; ++j) acc[i][j] += a[i] * bb[j];
   }
   __syncthreads();
-  for (int i = 0; i < 4; ++i)
-    for (int j = 0; j < 4; ++j) {
-      int r = ty * 4 + i, cc = tx * 4 + j;
+#pragma unroll
+  for (int i = 0; i < R; ++i)
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+      int r = ty * R + i, cc = tx * R + j;
       if (r < ni && cc < nb) A[(long long)(i0 + r) * ld + p0 + cc] = -acc[i][j];
     }
+}
+
+// ------------------------------------------------------------------------------ FP32 tile GEMM
+// acc (128 x 128 per CTA, 8 x 8 per thread) = A[rows, 0:K) * B[0:K, cols], both row-major FP32.
+// K is staged through shared memory in chunks of 32, double-buffered: the next chunk is fetched
+// into registers while the current one is multiplied.  A is stored k-major in shared memory so that
+// every thread reads its 8 rows as two float4; B is stored as is.  Thread (ty, tx) owns rows
+// {4ty..4ty+3, 64+4ty..64+4ty+3} and the same pattern of columns in tx.
+constexpr int MT = 128;
+constexpr int KC = 32;
+constexpr int SROW = MT + 4;   // 16-byte aligned rows; k-major stores of A hit distinct banks
+
+struct MmSmem {
+  float a[2][KC][SROW];
+  float b[2][KC][SROW];
+};
+
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc, int src_bytes) {
+  unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(gsrc), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// rows_ok: rows of A that may be read (row < rows_ok); a_cols_ok: columns of A that may be read;
+// cols_ok: columns of B that may be read; K: length of the contraction (A columns and B rows past K
+// count as zero).  lda, ldb, a_cols_ok, cols_ok multiples of 4; A, B 16-byte aligned.
+// B goes to shared memory by cp.async (zero-filled outside the valid range); A passes through
+// registers because it is transposed on the way.
+__device__ __forceinline__ void mm128_mainloop(const float* __restrict__ A, long long lda, int rows_ok,
+                                               const float* __restrict__ B, long long ldb, int cols_ok, int K,
+                                               int a_cols_ok, float acc[8][8], MmSmem& sm) {
+  const int tid = threadIdx.x;
+  const int ty = tid / 16, tx = tid % 16;
+  float4 ra[4];
+  auto fetch = [&](int c0, int st) {
+#pragma unroll
+    for (int rep = 0; rep < 4; ++rep) {
+      int q = tid + rep * 256;
+      // A: row i, four consecutive k starting at kq
+      int i = q % MT, kq = (q / MT) * 4;
+      int kg = c0 + kq;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (i < rows_ok && kg < a_cols_ok) {
+        v = *reinterpret_cast<const float4*>(A + (long long)i * lda + kg);
+        if (kg + 0 >= K) v.x = 0.f;
+        if (kg + 1 >= K) v.y = 0.f;
+        if (kg + 2 >= K) v.z = 0.f;
+        if (kg + 3 >= K) v.w = 0.f;
+      }
+      ra[rep] = v;
+      // B: row kk, four consecutive columns, straight to shared memory
+      int kk = q / 32, c = (q % 32) * 4;
+      bool ok = (c0 + kk < K) && (c < cols_ok);
+      const float* src = ok ? B + (long long)(c0 + kk) * ldb + c : B;
+      cp_async16(&sm.b[st][kk][c], src, ok ? 16 : 0);
+    }
+    cp_async_commit();
+  };
+  auto stash = [&](int st) {
+#pragma unroll
+    for (int rep = 0; rep < 4; ++rep) {
+      int q = tid + rep * 256;
+      int i = q % MT, kq = (q / MT) * 4;
+      sm.a[st][kq + 0][i] = ra[rep].x;
+      sm.a[st][kq + 1][i] = ra[rep].y;
+      sm.a[st][kq + 2][i] = ra[rep].z;
+      sm.a[st][kq + 3][i] = ra[rep].w;
+    }
+  };
+  const int nchunk = (K + KC - 1) / KC;
+  fetch(0, 0);
+  stash(0);
+  cp_async_wait_all();
+  __syncthreads();
+  for (int ch = 0; ch < nchunk; ++ch) {
+    const int st = ch & 1;
+    if (ch + 1 < nchunk) fetch((ch + 1) * KC, st ^ 1);
+#pragma unroll 8
+    for (int kk = 0; kk < KC; ++kk) {
+      float4 a0 = *reinterpret_cast<const float4*>(&sm.a[st][kk][ty * 4]);
+      float4 a1 = *reinterpret_cast<const float4*>(&sm.a[st][kk][64 + ty * 4]);
+      float4 b0 = *reinterpret_cast<const float4*>(&sm.b[st][kk][tx * 4]);
+      float4 b1 = *reinterpret_cast<const float4*>(&sm.b[st][kk][64 + tx * 4]);
+      const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+      const float bb[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], bb[j], acc[i][j]);
+    }
+    if (ch + 1 < nchunk) {
+      stash(st ^ 1);
+      cp_async_wait_all();
+    }
+    __syncthreads();
+  }
+}
+
+__device__ __forceinline__ int mm_row(int ty, int i) { return (i < 4) ? ty * 4 + i : 64 + ty * 4 + (i - 4); }
+
+// Gauss-Jordan trailing update, FP32, panel width 128: A[I, J] -= A[I, P] * A[P, J] for I, J != k.
+// Rows and columns are processed up to the padded leading dimension (padding is zero and stays so).
+__global__ void __launch_bounds__(256, 2) k_mm128_gj_update(int k, int cnt, const int* __restrict__ order,
+                                                            const long long* __restrict__ pre2,
+                                                            const int* __restrict__ bn, const int* __restrict__ bld,
+                                                            const long long* __restrict__ moff, float* __restrict__ mat) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  MmSmem& sm = *reinterpret_cast<MmSmem*>(smraw);
+  long long w = blockIdx.x;
+  int s = find_block(pre2, cnt, w);
+  int b = order[s];
+  int n = bn[b], ld = bld[b];
+  int T = (n + MT - 1) / MT;
+  long long loc = w - pre2[s];
+  int it = tile_skip((int)(loc / (T - 1)), k), jt = tile_skip((int)(loc % (T - 1)), k);
+  int p0 = k * MT, i0 = it * MT, j0 = jt * MT;
+  int nb = min(MT, n - p0);
+  int rows_ok = min(MT, ld - i0), cols_ok = min(MT, ld - j0);
+  float* Ab = mat + moff[b];
+  float acc[8][8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+  mm128_mainloop(Ab + (long long)i0 * ld + p0, ld, rows_ok, Ab + (long long)p0 * ld + j0, ld, cols_ok, nb,
+                 ld - p0, acc, sm);
+  const int ty = threadIdx.x / 16, tx = threadIdx.x % 16;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    int r = mm_row(ty, i);
+    if (r >= rows_ok) continue;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      int c = h * 64 + tx * 4;
+      if (c >= cols_ok) continue;
+      float4* q = reinterpret_cast<float4*>(Ab + (long long)(i0 + r) * ld + j0 + c);
+      float4 v = *q;
+      v.x -= acc[i][h * 4 + 0];
+      v.y -= acc[i][h * 4 + 1];
+      v.z -= acc[i][h * 4 + 2];
+      v.w -= acc[i][h * 4 + 3];
+      *q = v;
+    }
+  }
+}
+
+// Newton-Schulz product T = X * R per entry (n x n, FP32, 128 x 128 tiles over the padded ld).
+__global__ void __launch_bounds__(256, 2) k_mm128_ns(const int* __restrict__ lst, const long long* __restrict__ tilepre,
+                                                     int nent, const int* __restrict__ bn, const int* __restrict__ bld,
+                                                     const long long* __restrict__ moff, const float* __restrict__ mat,
+                                                     const long long* __restrict__ soff, const float* __restrict__ R,
+                                                     float* __restrict__ Tout) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  MmSmem& sm = *reinterpret_cast<MmSmem*>(smraw);
+  long long w = blockIdx.x;
+  int e = find_block(tilepre, nent, w);
+  int b = lst[e];
+  int n = bn[b], ld = bld[b];
+  int T = (n + MT - 1) / MT;
+  long long loc = w - tilepre[e];
+  int it = (int)(loc / T), jt = (int)(loc % T);
+  int i0 = it * MT, j0 = jt * MT;
+  int rows_ok = min(MT, ld - i0), cols_ok = min(MT, ld - j0);
+  const float* X = mat + moff[b];
+  const float* Rm = R + soff[e];
+  float acc[8][8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+  mm128_mainloop(X + (long long)i0 * ld, ld, rows_ok, Rm + j0, ld, cols_ok, n, ld, acc, sm);
+  float* To = Tout + soff[e];
+  const int ty = threadIdx.x / 16, tx = threadIdx.x % 16;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    int r = mm_row(ty, i);
+    if (r >= rows_ok) continue;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      int c = h * 64 + tx * 4;
+      if (c >= cols_ok) continue;
+      *reinterpret_cast<float4*>(To + (long long)(i0 + r) * ld + j0 + c) =
+          make_float4(acc[i][h * 4 + 0], acc[i][h * 4 + 1], acc[i][h * 4 + 2], acc[i][h * 4 + 3]);
+    }
+  }
 }
 
 // ------------------------------------------------------------------------------ closure RHS
@@ -800,14 +1011,19 @@ cudaError_t launch_assemble(const Ctx& C, const BlockSet& B, int op, const doubl
 template cudaError_t launch_assemble<double>(const Ctx&, const BlockSet&, int, const double*, double*, int);
 template cudaError_t launch_assemble<float>(const Ctx&, const BlockSet&, int, const double*, float*, int);
 
+template <typename ST> struct GjPanel;
+template <> struct GjPanel<double> { static constexpr int tb = 64; };
+template <> struct GjPanel<float> { static constexpr int tb = MT; };
+
 template <typename ST>
 cudaError_t launch_gj_invert(const BlockSet& B, ST* mat, int* d_bad, cudaStream_t s) {
   if (B.nblk == 0) return cudaSuccess;
+  constexpr int TBK = GjPanel<ST>::tb;
   // order blocks by tile count (descending): the active set at step k is a prefix
   std::vector<int> order(B.nblk);
   for (int i = 0; i < B.nblk; ++i) order[i] = i;
   std::vector<int> T(B.nblk);
-  for (int i = 0; i < B.nblk; ++i) T[i] = (B.n[i] + TB - 1) / TB;
+  for (int i = 0; i < B.nblk; ++i) T[i] = (B.n[i] + TBK - 1) / TBK;
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return T[a] > T[b]; });
   std::vector<long long> pre1(B.nblk + 1, 0), pre2(B.nblk + 1, 0);
   for (int s2 = 0; s2 < B.nblk; ++s2) {
@@ -826,23 +1042,37 @@ cudaError_t launch_gj_invert(const BlockSet& B, ST* mat, int* d_bad, cudaStream_
   cudaMemcpyAsync(d_order, order.data(), sizeof(int) * B.nblk, cudaMemcpyHostToDevice, s);
   cudaMemcpyAsync(d_pre1, pre1.data(), sizeof(long long) * (B.nblk + 1), cudaMemcpyHostToDevice, s);
   cudaMemcpyAsync(d_pre2, pre2.data(), sizeof(long long) * (B.nblk + 1), cudaMemcpyHostToDevice, s);
-  size_t smem = 2 * sizeof(ST) * TB * (TB + 1);
-  cudaFuncSetAttribute(k_gj_rowpanel<ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  cudaFuncSetAttribute(k_gj_update<ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  cudaFuncSetAttribute(k_gj_colpanel<ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const size_t smem_diag = sizeof(ST) * TBK * (TBK + 1) + sizeof(ST) * TBK;
+  const size_t smem = 2 * sizeof(ST) * TBK * (TBK + 1);
+  const size_t smem_mm = sizeof(MmSmem);
+  cudaFuncSetAttribute(k_gj_diag<ST, TBK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_diag);
+  cudaFuncSetAttribute(k_gj_rowpanel<ST, TBK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaFuncSetAttribute(k_gj_colpanel<ST, TBK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (std::is_same<ST, float>::value)
+    cudaFuncSetAttribute(k_mm128_gj_update, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_mm);
+  else
+    cudaFuncSetAttribute(k_gj_update<ST, TBK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int Tmax = T[order[0]];
   int cnt = B.nblk;
   for (int k = 0; k < Tmax; ++k) {
     while (cnt > 0 && T[order[cnt - 1]] <= k) --cnt;
-    { pns::count_launch(); k_gj_diag<ST><<<cnt, 256, 0, s>>>(k, d_order, B.d_n.as<int>(), B.d_ld.as<int>(), B.d_moff.as<long long>(), mat,
-                                      d_bad); }
+    { pns::count_launch(); k_gj_diag<ST, TBK><<<cnt, 256, smem_diag, s>>>(k, d_order, B.d_n.as<int>(), B.d_ld.as<int>(),
+                                                                         B.d_moff.as<long long>(), mat, d_bad); }
     if (pre1[cnt] > 0) {
-      { pns::count_launch(); k_gj_rowpanel<ST><<<(unsigned)pre1[cnt], 256, smem, s>>>(k, cnt, d_order, d_pre1, B.d_n.as<int>(),
+      { pns::count_launch(); k_gj_rowpanel<ST, TBK><<<(unsigned)pre1[cnt], 256, smem, s>>>(k, cnt, d_order, d_pre1, B.d_n.as<int>(),
                                                                B.d_ld.as<int>(), B.d_moff.as<long long>(), mat); }
-      if (pre2[cnt] > 0)
-        { pns::count_launch(); k_gj_update<ST><<<(unsigned)pre2[cnt], 256, smem, s>>>(k, cnt, d_order, d_pre2, B.d_n.as<int>(),
-                                                               B.d_ld.as<int>(), B.d_moff.as<long long>(), mat); }
-      { pns::count_launch(); k_gj_colpanel<ST><<<(unsigned)pre1[cnt], 256, smem, s>>>(k, cnt, d_order, d_pre1, B.d_n.as<int>(),
+      if (pre2[cnt] > 0) {
+        if constexpr (std::is_same<ST, float>::value) {
+          pns::count_launch();
+          k_mm128_gj_update<<<(unsigned)pre2[cnt], 256, smem_mm, s>>>(k, cnt, d_order, d_pre2, B.d_n.as<int>(),
+                                                                      B.d_ld.as<int>(), B.d_moff.as<long long>(), mat);
+        } else {
+          pns::count_launch();
+          k_gj_update<ST, TBK><<<(unsigned)pre2[cnt], 256, smem, s>>>(k, cnt, d_order, d_pre2, B.d_n.as<int>(),
+                                                                      B.d_ld.as<int>(), B.d_moff.as<long long>(), mat);
+        }
+      }
+      { pns::count_launch(); k_gj_colpanel<ST, TBK><<<(unsigned)pre1[cnt], 256, smem, s>>>(k, cnt, d_order, d_pre1, B.d_n.as<int>(),
                                                                B.d_ld.as<int>(), B.d_moff.as<long long>(), mat); }
     }
     if ((e = cudaGetLastError()) != cudaSuccess) break;
@@ -913,8 +1143,11 @@ cudaError_t launch_ns_refine(const Ctx& C, const BlockSet& B, int op, const doub
   cudaError_t e = cudaSuccess;
   *max_before = 0;
   if (max_after) *max_after = 0;
-  size_t smem = 2 * sizeof(AT) * TB * (TB + 1);
-  cudaFuncSetAttribute(k_ns_gemm<ST, AT, AT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  constexpr bool f32 = std::is_same<ST, float>::value && std::is_same<AT, float>::value;
+  constexpr int NT = f32 ? MT : TB;   // tile edge of the product T = X R
+  size_t smem = f32 ? sizeof(MmSmem) : 2 * sizeof(AT) * TB * (TB + 1);
+  if (f32) cudaFuncSetAttribute(k_mm128_ns, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  else cudaFuncSetAttribute(k_ns_gemm<ST, AT, AT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   // chunks of consecutive blocks whose R and T fit the budget
   int b0 = 0;
   while (b0 < B.nblk && e == cudaSuccess) {
@@ -976,7 +1209,7 @@ cudaError_t launch_ns_refine(const Ctx& C, const BlockSet& B, int op, const doub
         int ns = (int)sel.size();
         std::vector<long long> tpre(ns + 1, 0), epre(ns + 1, 0);
         for (int q = 0; q < ns; ++q) {
-          long long Tt = (B.n[sel[q]] + TB - 1) / TB;
+          long long Tt = (B.n[sel[q]] + NT - 1) / NT;
           tpre[q + 1] = tpre[q] + Tt * Tt;
           epre[q + 1] = epre[q] + (long long)B.ld[sel[q]] * B.ld[sel[q]];
         }
@@ -991,9 +1224,16 @@ cudaError_t launch_ns_refine(const Ctx& C, const BlockSet& B, int op, const doub
         cudaMemcpyAsync(d_tpre, tpre.data(), sizeof(long long) * (ns + 1), cudaMemcpyHostToDevice, s);
         cudaMemcpyAsync(d_epre, epre.data(), sizeof(long long) * (ns + 1), cudaMemcpyHostToDevice, s);
         cudaMemcpyAsync(d_ssoff, ssoff.data(), sizeof(long long) * (ns + 1), cudaMemcpyHostToDevice, s);
-        { pns::count_launch(); k_ns_gemm<ST, AT, AT><<<(unsigned)tpre[ns], 256, smem, s>>>(d_sel, d_tpre, ns, B.d_n.as<int>(),
-                                                                   B.d_ld.as<int>(), B.d_moff.as<long long>(), mat,
-                                                                   d_ssoff, R, T); }
+        if constexpr (f32) {
+          pns::count_launch();
+          k_mm128_ns<<<(unsigned)tpre[ns], 256, smem, s>>>(d_sel, d_tpre, ns, B.d_n.as<int>(), B.d_ld.as<int>(),
+                                                           B.d_moff.as<long long>(), mat, d_ssoff, R, T);
+        } else {
+          pns::count_launch();
+          k_ns_gemm<ST, AT, AT><<<(unsigned)tpre[ns], 256, smem, s>>>(d_sel, d_tpre, ns, B.d_n.as<int>(),
+                                                                     B.d_ld.as<int>(), B.d_moff.as<long long>(), mat,
+                                                                     d_ssoff, R, T);
+        }
         { pns::count_launch(); k_ns_add<ST, AT><<<(unsigned)((epre[ns] + 255) / 256), 256, 0, s>>>(
             d_sel, d_epre, ns, B.d_n.as<int>(), B.d_ld.as<int>(), B.d_moff.as<long long>(), mat, d_ssoff, T); }
         e = cudaStreamSynchronize(s);
