@@ -45,6 +45,9 @@ def parse():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--compare", default="",
+                    help="comma-separated preconditioner variants to time once each after the main run "
+                         "(e.g. gplmm,aplmm_ns,aplmm_s,block_schur); results go to the 'variants' key")
     return ap.parse_args()
 
 
@@ -193,6 +196,31 @@ print(json.dumps({"total_s": total, "maps_s": t_maps, "asm_s": t_asm, "build_s":
                        f"iteration {d['iter_s']:.2f} s; total = maps + 2 builds + {its_total} iterations")}
 
 
+def compare_variants(args, w, mu):
+    """One solve per named variant on the same workload (fresh context each): wall time on the
+    library's stream, iteration counts, build time."""
+    import torch
+    from paper_2510_22077_gb300 import pns
+    out = {}
+    for var in [v.strip() for v in args.compare.split(",") if v.strip()]:
+        S = pns.Solver(w.mask, w.labels, 1.0, mu, (1.0, 0.0, 0.0), variant=var, precision=args.precision,
+                       timing=True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(S.stream)
+        x = S.zeros()
+        _, sst = S.pns_stokes_solve(x)
+        S.pns_build_precond(x)
+        st = S.pns_newton_solve(x, check=False)
+        e1.record(S.stream)
+        torch.cuda.synchronize()
+        out[var] = {"ms": e0.elapsed_time(e1), "status": st["status"], "newton_its": st["newton_its"],
+                    "fgmres_its_stokes": sst["fgmres_its_total"], "fgmres_its_newton": st["fgmres_its"],
+                    "t_build_ms": st["t_ml_ms"] + st["t_mg_ms"], "final_res": st["res_hist"][-1] if st["res_hist"] else None}
+        S.close()
+    return out
+
+
 # ---------------------------------------------------------------------------------------- main
 def main():
     args = parse()
@@ -291,6 +319,8 @@ def main():
         S2.close()
         line["e2e"] = {"value": e2e_ms, "unit": UNIT, "h2d_bytes_per_step": int(w.mask.nbytes + w.labels.nbytes),
                        "d2h_bytes_per_step": int(host.nbytes)}
+    if rank == 0 and args.compare:
+        line["variants"] = compare_variants(args, w, mu)
     if rank == 0 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(w, mu, its_stokes + its_newton)
     if rank == 0:

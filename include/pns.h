@@ -61,8 +61,14 @@ enum pns_status {
  *            wind w = velocity of the linearisation state, inertia removed on tagged faces;
  *   APLMM_NS build matrix = Newton Jacobian at the linearisation state;
  *   APLMM_S  build matrix = Stokes Jacobian (inertia dropped, rho/dt kept);
- *   ML_ONLY  the dual-primary smoother alone (Eq. 24) built from the gPLMM matrix (no M_G). */
-enum pns_variant { PNS_GPLMM = 0, PNS_APLMM_NS = 1, PNS_APLMM_S = 2, PNS_ML_ONLY = 3 };
+ *   ML_ONLY  the dual-primary smoother alone (Eq. 24) built from the gPLMM matrix (no M_G);
+ *   BLOCK_SCHUR  the block-triangular comparator of Sec. 1, M_B = [[F, B1], [0, X]] with X^{-1} the
+ *            scaled BFBt approximation of the Schur complement (Eq. 4), D = diag(F); built from the
+ *            Newton Jacobian at the linearisation state.  Its solves with F and with B2 D^{-1} B1 run
+ *            GMRES (block_inner_its iterations at most, relative tolerance block_inner_tol) with block
+ *            Jacobi over the pores (dense inverses in the storage precision; BF16 stores FP32).
+ *            The preconditioner is then not a fixed linear map: FGMRES is what allows that. */
+enum pns_variant { PNS_GPLMM = 0, PNS_APLMM_NS = 1, PNS_APLMM_S = 2, PNS_ML_ONLY = 3, PNS_BLOCK_SCHUR = 4 };
 
 /* Storage / arithmetic precision of the preconditioner (local inverses, basis, coarse inverse,
  * inner residual updates).  The Newton residual, the outer Jacobian, Arnoldi and Givens are FP64. */
@@ -90,6 +96,8 @@ typedef struct pns_options {
                             -1 = automatic (up to 3 for FP32/BF16; FP64 inverts in FP64) */
   int timing;            /* 1: record CUDA events around the local-solve kernels (pns_stats) */
   void* stream;          /* cudaStream_t to enqueue on (NULL = legacy default stream) */
+  int block_inner_its;   /* PNS_BLOCK_SCHUR: inner GMRES iterations per solve with F or L (default 20) */
+  double block_inner_tol;/* PNS_BLOCK_SCHUR: inner GMRES relative tolerance (default 1e-2) */
 } pns_options;
 
 typedef struct pns_stats {
@@ -154,7 +162,8 @@ int pns_operator_apply(pns_ctx* ctx, int variant, const double* x_lin, const dou
 /* Build the preconditioner of opt.variant at the linearisation state x_lin (device, full layout):
  * local blocks of the primary and dual grids (Eq. 25) assembled densely and inverted, closure
  * blocks (Eqs. 6 and 9), shape and correction vectors (Eqs. 15 and 17), coarse matrix
- * A^o = R^ A_b P^ (Remark 1) and its inverse.  Synchronises. */
+ * A^o = R^ A_b P^ (Remark 1) and its inverse.  For APLMM_S the build matrix does not depend on
+ * x_lin, so a built aPLMM_S preconditioner is kept and the call returns at once.  Synchronises. */
 int pns_build_precond(pns_ctx* ctx, const double* x_lin);
 
 /* z = M^{-1} v (Eqs. 4a, 24, 25, 20): FP64 in and out, internal precision opt.precision.
@@ -179,8 +188,10 @@ int pns_precond_apply_static(pns_ctx* ctx, const double* v, double* z);
 int pns_newton_solve(pns_ctx* ctx, double* x, const double* x_prev, pns_stats* st);
 
 /* Stokes solution (inertia dropped, rho b kept): the initial Newton iterate of Sec. 4 when no
- * nearby wind exists.  Builds an aPLMM_S preconditioner internally (kept separately from the one
- * of pns_build_precond) and runs FGMRES on the linear system.  x: device, output.  Synchronises. */
+ * nearby wind exists.  Builds an aPLMM_S preconditioner and runs FGMRES on the linear system.
+ * When the context's variant is APLMM_S that preconditioner becomes the context's own (Newton then
+ * uses it without a second build); otherwise it is temporary and the context's preconditioner is
+ * left as it was.  x: device, output.  Synchronises. */
 int pns_stokes_solve(pns_ctx* ctx, double* x, pns_stats* st);
 
 /* Copy the inverse of the coarse matrix A^o = R^ A_b P^ (Remark 1) of the built preconditioner to a

@@ -53,6 +53,19 @@ struct BlockSet {
   DevBuf items;                  // int4
 };
 
+// Block-triangular Schur comparator (variant PNS_BLOCK_SCHUR): pore blocks of F and L = B2 D^-1 B1 for
+// block Jacobi, D = diag(F), and the workspace of its inner GMRES.
+struct BlockSchurData {
+  BlockSet bf, bl;               // pore blocks of F (faces) and of L (cells that are not pinned)
+  DevBuf D;                      // diag(F) on faces, full layout
+  int its = 20;                  // inner GMRES iterations (no restart)
+  double tol = 1e-2;             // inner GMRES relative tolerance
+  DevBuf V, Z, H, small, partial;
+  DevBuf t1, t2, t3, t4, t5;     // full-layout temporaries
+  DevBuf pk;                     // packed local vectors of the block-Jacobi solves
+  long long inner_total = 0;     // inner iterations since the build
+};
+
 // Preconditioner built from one build matrix A_b (pns_build_precond / the internal Stokes solve).
 struct Precond {
   bool built = false;
@@ -75,6 +88,7 @@ struct Precond {
   DevBuf seg_items;              // int2 (segment, chunk start) work list
   double local_bytes = 0;        // algorithmic bytes of one M_d + M_p pass
   double ns_residual_before = 0; // max |I - A X| of the local inverses before refinement
+  BlockSchurData bs;             // variant PNS_BLOCK_SCHUR only
 };
 
 struct Ctx {
@@ -158,6 +172,15 @@ struct Woodbury {
   cudaError_t apply(const Ctx& C, const BlockSet& B, const ST* X, const double* R, double* S, double* Y,
                     const long long* d_roff, const int* d_kc, const std::vector<int>& kc);
 };
+
+// block-triangular Schur comparator (kernels_block.cu)
+cudaError_t launch_diag_F(const Ctx& C, int op, const double* state, double* D);
+cudaError_t launch_grad(const Ctx& C, const double* y, const double* D, const double* v, int mode, double* t);
+cudaError_t launch_div(const Ctx& C, const double* t, const double* D, double sign, double* y);
+cudaError_t launch_compose(const Ctx& C, const double* a, const double* b, int mode, double* out);
+cudaError_t launch_zero_cells(const Ctx& C, double* y);
+template <typename ST>
+cudaError_t launch_assemble_L(const Ctx& C, const BlockSet& B, const double* D, ST* mat);
 
 // coarse
 cudaError_t launch_seg_sum(const Precond& pc, const void* v, int vt_is_double, double* out, cudaStream_t s);

@@ -29,6 +29,7 @@ int build_maps(const Geo& G, const uint8_t* mask, const int32_t* labels, int n_d
   const int nc = G.ncell, dim = G.dim;
   const long long nfull = (long long)(dim + 1) * nc;
   M.flags.assign(nc, 0);
+  M.label.assign(labels, labels + nc);
   for (int c = 0; c < nc; ++c) {
     bool v = mask[c] != 0;
     if (v && labels[c] < 1) { err = "labels must be >= 1 on void cells"; return -1; }

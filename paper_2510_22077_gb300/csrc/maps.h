@@ -11,6 +11,7 @@ namespace pns {
 
 struct Maps {
   std::vector<uint8_t> flags;             // per cell, see stencil.cuh
+  std::vector<int> label;                 // per cell: the input pore label (0 on solid)
   std::vector<int> pins;                  // ascending
   std::vector<int> cell_prim;             // per cell: primary grid or -1
   std::vector<int> cell_iface;            // per cell: contact interface or -1

@@ -124,6 +124,7 @@ int make_blockset(Ctx& C, BlockSet& B, const std::vector<std::vector<int>>& list
 int op_of_variant(int variant) {
   switch (variant) {
     case PNS_APLMM_NS: return OP_NEWTON;
+    case PNS_BLOCK_SCHUR: return OP_NEWTON;
     case PNS_APLMM_S: return OP_STOKES;
     default: return OP_OSEEN;
   }
@@ -362,6 +363,192 @@ int ensure_scratch(Ctx& C, const Precond& pc) {
   return PNS_OK;
 }
 
+// --------------------------------------------------------------------------- block comparator
+// Block-triangular Schur-complement preconditioner (Sec. 1, M_B with the scaled BFBt X of Eq. 4).
+// Pore partition: a face unknown belongs to the pore of the cell on its high side (the cell that
+// stores it), a cell to its own pore; pinned cells are left out of L.
+template <typename ST>
+int build_block_t(Ctx& C, Precond& pc, int* d_bad) {
+  BlockSchurData& S = pc.bs;
+  const cudaStream_t s = C.stream;
+  const Maps& M = C.M;
+  const int nc = C.G.ncell, dim = C.G.dim;
+  int maxlab = 0;
+  for (int c = 0; c < nc; ++c) maxlab = std::max(maxlab, M.label[c]);
+  std::vector<int> pid(maxlab + 1, -1);
+  int np = 0;
+  for (int c = 0; c < nc; ++c)
+    if ((M.flags[c] & FL_VOID) && pid[M.label[c]] < 0) pid[M.label[c]] = np++;
+  std::vector<std::vector<int>> lf(np), lc(np);
+  for (int d = 0; d < dim; ++d)
+    for (int c = 0; c < nc; ++c)
+      if (M.flags[c] & fl_face(d)) lf[pid[M.label[c]]].push_back(d * nc + c);
+  for (int c = 0; c < nc; ++c)
+    if ((M.flags[c] & FL_VOID) && !(M.flags[c] & FL_PIN)) lc[pid[M.label[c]]].push_back(dim * nc + c);
+  auto drop_empty = [](std::vector<std::vector<int>>& l) {
+    l.erase(std::remove_if(l.begin(), l.end(), [](const std::vector<int>& v) { return v.empty(); }), l.end());
+  };
+  drop_empty(lf);
+  drop_empty(lc);
+  CKS(make_blockset(C, S.bf, lf));
+  CKS(make_blockset(C, S.bl, lc));
+  CK(dalloc(S.D, sizeof(double) * C.nfull));
+  CK(launch_diag_F(C, OP_NEWTON, pc.state.as<double>(), S.D.as<double>()));
+  if (S.bf.nblk) {
+    CK(dalloc(S.bf.mat, sizeof(ST) * S.bf.m_total));
+    CK(launch_assemble<ST>(C, S.bf, OP_NEWTON, pc.state.as<double>(), S.bf.mat.as<ST>(), 0));
+    CK(launch_gj_invert<ST>(S.bf, S.bf.mat.as<ST>(), d_bad, s));
+  }
+  if (S.bl.nblk) {
+    CK(dalloc(S.bl.mat, sizeof(ST) * S.bl.m_total));
+    CK(launch_assemble_L<ST>(C, S.bl, S.D.as<double>(), S.bl.mat.as<ST>()));
+    CK(launch_gj_invert<ST>(S.bl, S.bl.mat.as<ST>(), d_bad, s));
+  }
+  S.its = C.opt.block_inner_its;
+  S.tol = C.opt.block_inner_tol;
+  const size_t vb = sizeof(double) * C.nfull;
+  CK(dalloc(S.V, vb * (S.its + 1)));
+  CK(dalloc(S.Z, vb * S.its));
+  CK(dalloc(S.H, sizeof(double) * (S.its + 1) * S.its));
+  CK(dalloc(S.small, sizeof(double) * (7 * (S.its + 1) + 8)));
+  CK(dalloc(S.partial, sizeof(double) * 1024 * (S.its + 2)));
+  for (DevBuf* t : {&S.t1, &S.t2, &S.t3, &S.t4, &S.t5}) CK(dalloc(*t, vb));
+  CK(dalloc(S.pk, sizeof(ST) * std::max(1LL, std::max(S.bf.n_total, S.bl.n_total))));
+  S.inner_total = 0;
+  return PNS_OK;
+}
+
+int build_block(Ctx& C, Precond& pc) {
+  DevBuf bad;
+  CK(dalloc(bad, sizeof(int)));
+  double t0 = now_ms();
+  if (pc.precision == PNS_FP64) CKS(build_block_t<double>(C, pc, bad.as<int>()));
+  else CKS(build_block_t<float>(C, pc, bad.as<int>()));
+  CK(cudaStreamSynchronize(C.stream));
+  C.t_ml_ms = now_ms() - t0;
+  C.t_mg_ms = 0;
+  int hbad = 0;
+  CK(cudaMemcpy(&hbad, bad.p, sizeof(int), cudaMemcpyDeviceToHost));
+  if (hbad) return fail(C, PNS_ERR_SINGULAR, "zero or non-finite pivot in a block-Jacobi factor");
+  pc.local_bytes = 0;
+  for (BlockSet* B : {&pc.bs.bf, &pc.bs.bl})
+    for (int b = 0; b < B->nblk; ++b)
+      pc.local_bytes += (double)B->n[b] * B->ld[b] * (pc.precision == PNS_FP64 ? 8 : 4) + 20.0 * B->n[b];
+  pc.built = true;
+  return PNS_OK;
+}
+
+// z = M^{-1} r by block Jacobi over one block set of the comparator (z zero outside the set)
+int block_jacobi(Ctx& C, Precond& pc, const BlockSet& B, const double* r, double* z) {
+  CK(cudaMemsetAsync(z, 0, sizeof(double) * C.nfull, C.stream));
+  if (B.nblk == 0) return PNS_OK;
+  if (pc.precision == PNS_FP64)
+    CK((launch_local_solve<double, double>(B, B.mat.as<double>(), r, z, pc.bs.pk.as<double>(), 0, C.stream)));
+  else
+    CK((launch_local_solve<float, float>(B, B.mat.as<float>(), r, z, pc.bs.pk.as<float>(), 0, C.stream)));
+  return PNS_OK;
+}
+
+// y = F v (faces; the cell block of v is zero, the cell block of y is zeroed)
+int block_opF(Ctx& C, Precond& pc, const double* v, double* y) {
+  CK(launch_apply<double>(C, OP_NEWTON, pc.state.as<double>(), v, nullptr, y, true));
+  CK(launch_zero_cells(C, y));
+  return PNS_OK;
+}
+
+// y = L v = B2 D^{-1} B1 v on the cells that are not pinned
+int block_opL(Ctx& C, Precond& pc, const double* v, double* y) {
+  double* t = pc.bs.t5.as<double>();
+  CK(launch_grad(C, v, pc.bs.D.as<double>(), nullptr, 0, t));
+  CK(launch_div(C, t, nullptr, 1.0, y));
+  return PNS_OK;
+}
+
+// Inner GMRES (FP64 vectors, classical Gram-Schmidt twice, no restart): x ~ A^{-1} b with block
+// Jacobi on the right; stops after S.its iterations or at ||b - A x|| <= S.tol ||b||.
+int block_gmres(Ctx& C, Precond& pc, int which, const double* b, double* x) {
+  BlockSchurData& S = pc.bs;
+  const cudaStream_t s = C.stream;
+  const long long n = C.nfull;
+  const int m = S.its;
+  double* V = S.V.as<double>();
+  double* Z = S.Z.as<double>();
+  double* H = S.H.as<double>();
+  double* cs = S.small.as<double>();
+  double* sn = cs + (m + 1);
+  double* g = sn + (m + 1);
+  double* outv = g + (m + 1);
+  double* h1 = outv + 8;
+  double* h2 = h1 + (m + 1);
+  double* yv = h2 + (m + 1);
+  double* nrm = yv + (m + 1);
+  double* partial = S.partial.as<double>();
+  const BlockSet& B = which == 0 ? S.bf : S.bl;
+  CK(cudaMemsetAsync(x, 0, sizeof(double) * n, s));
+  CK(launch_dot(b, b, n, partial, nrm, s));
+  double beta2 = 0;
+  CK(cudaMemcpyAsync(&beta2, nrm, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  const double beta = std::sqrt(beta2);
+  if (!std::isfinite(beta)) return fail(C, PNS_ERR_NAN, "non-finite vector in the block comparator");
+  if (beta == 0.0) return PNS_OK;
+  const double tol_abs = S.tol * beta;
+  std::vector<double> gh(m + 1, 0.0);
+  gh[0] = beta;
+  CK(cudaMemcpyAsync(g, gh.data(), sizeof(double) * (m + 1), cudaMemcpyHostToDevice, s));
+  CK(cudaMemsetAsync(H, 0, sizeof(double) * (size_t)(m + 1) * m, s));
+  CK(cudaMemcpyAsync(V, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  const double binv = 1.0 / beta;
+  CK(cudaMemcpyAsync(nrm, &binv, sizeof(double), cudaMemcpyHostToDevice, s));
+  CK(launch_scale(V, n, nrm, nullptr, 0, s));
+  int k = 0;
+  for (int j = 0; j < m; ++j) {
+    double* vj = V + (size_t)j * n;
+    double* zj = Z + (size_t)j * n;
+    double* w = V + (size_t)(j + 1) * n;
+    CKS(block_jacobi(C, pc, B, vj, zj));
+    if (which == 0) CKS(block_opF(C, pc, zj, w));
+    else CKS(block_opL(C, pc, zj, w));
+    CK(launch_multidot(V, n, j + 1, w, n, partial, 0, h1, s));
+    CK(launch_multi_axpy(w, V, n, j + 1, h1, -1.0, n, s));
+    CK(launch_multidot(V, n, j + 1, w, n, partial, 0, h2, s));
+    CK(launch_multi_axpy(w, V, n, j + 1, h2, -1.0, n, s));
+    CK(launch_dot(w, w, n, partial, nrm, s));
+    CK(launch_hcol(H, m, j, h1, h2, nrm, s));
+    CK(launch_scale(w, n, nullptr, nrm, 1, s));
+    CK(launch_givens(H, m, cs, sn, g, j, outv, s));
+    double hres[2];
+    CK(cudaMemcpyAsync(hres, outv, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    k = j + 1;
+    S.inner_total++;
+    if (!std::isfinite(hres[0])) return fail(C, PNS_ERR_NAN, "non-finite residual in the block comparator");
+    if (hres[0] <= tol_abs) break;
+  }
+  CK(launch_trisolve_update(H, m, g, k, yv, Z, n, x, n, s));
+  return PNS_OK;
+}
+
+// z = M_B^{-1} v:  y = X^{-1} v_p (pins: y = v),  u = F^{-1} (v_u - B1 y),  z = [u; y]
+int block_apply(Ctx& C, Precond& pc, const double* v, double* z) {
+  BlockSchurData& S = pc.bs;
+  double *t1 = S.t1.as<double>(), *t2 = S.t2.as<double>(), *t3 = S.t3.as<double>(), *t4 = S.t4.as<double>();
+  double* t5 = S.t5.as<double>();
+  const double* D = S.D.as<double>();
+  CK(launch_compose(C, v, nullptr, 0, t1));                    // v on the cells that are not pinned
+  CKS(block_gmres(C, pc, 1, t1, t2));                          // t2 = L^{-1} v_n
+  CK(launch_grad(C, t2, D, nullptr, 0, t3));                   // t3 = D^{-1} B1 t2
+  CK(launch_apply<double>(C, OP_NEWTON, pc.state.as<double>(), t3, nullptr, t4, true));   // F t3 (faces)
+  CK(launch_div(C, t4, D, 1.0, t1));                           // t1 = B2 D^{-1} F D^{-1} B1 t2
+  CKS(block_gmres(C, pc, 1, t1, t2));                          // t2 = L^{-1} t1 = -y_n
+  CK(launch_compose(C, v, t2, 1, t3));                         // t3 = y (pins: v)
+  CK(launch_grad(C, t3, nullptr, v, 1, t1));                   // t1 = v_u - B1 y
+  CKS(block_gmres(C, pc, 0, t1, t4));                          // t4 = F^{-1} t1
+  (void)t5;
+  CK(launch_compose(C, t4, t3, 2, z));                         // z = [t4; t3]
+  return PNS_OK;
+}
+
 int build_precond(Ctx& C, Precond& pc, int variant, const double* x_lin) {
   const cudaStream_t s = C.stream;
   pc.built = false;
@@ -375,6 +562,11 @@ int build_precond(Ctx& C, Precond& pc, int variant, const double* x_lin) {
   CK(dalloc(pc.state, sizeof(double) * C.nfull));
   if (x_lin) CK(cudaMemcpyAsync(pc.state.p, x_lin, sizeof(double) * C.nfull, cudaMemcpyDeviceToDevice, s));
   else CK(cudaMemsetAsync(pc.state.p, 0, sizeof(double) * C.nfull, s));
+  if (variant == PNS_BLOCK_SCHUR) {
+    pc.coarse = false;
+    pc.n_o = 0;
+    return build_block(C, pc);
+  }
   if (pc.prim.nblk != C.M.n_prim || pc.prim.idx.p == nullptr) CKS(make_blockset(C, pc.prim, C.M.prim_unk));
   if (pc.dual.nblk != C.M.n_iface || (C.M.n_iface && pc.dual.idx.p == nullptr)) CKS(make_blockset(C, pc.dual, C.M.dual_unk));
   CKS(build_segments(C, pc));
@@ -472,6 +664,7 @@ int precond_apply_impl(Ctx& C, Precond& pc, const double* v, double* z) {
 
 int precond_apply(Ctx& C, Precond& pc, const double* v, double* z) {
   if (!pc.built) return fail(C, PNS_ERR_STATE, "preconditioner not built");
+  if (pc.variant == PNS_BLOCK_SCHUR) return block_apply(C, pc, v, z);
   return precond_apply_impl(C, pc, v, z);
 }
 
@@ -666,6 +859,8 @@ void pns_default_options(pns_options* o) {
   o->refine_steps = -1;
   o->timing = 0;
   o->stream = nullptr;
+  o->block_inner_its = 20;
+  o->block_inner_tol = 1e-2;
 }
 
 int pns_setup(pns_ctx** out, int nz, int ny, int nx, const uint8_t* mask, const int32_t* labels, double rho,
@@ -680,7 +875,8 @@ int pns_setup(pns_ctx** out, int nz, int ny, int nx, const uint8_t* mask, const 
   if (opt) C.opt = *opt;
   else pns_default_options(&C.opt);
   if (C.opt.restart < 1 || C.opt.restart > 127 || C.opt.n_dilate < 0 || C.opt.n_tag < 1 || C.opt.precision < 0 ||
-      C.opt.precision > 2 || C.opt.variant < 0 || C.opt.variant > 3) {
+      C.opt.precision > 2 || C.opt.variant < 0 || C.opt.variant > 4 || C.opt.block_inner_its < 1 ||
+      C.opt.block_inner_its > 100 || !(C.opt.block_inner_tol > 0.0)) {
     delete ctx;
     return PNS_ERR_ARG;
   }
@@ -794,6 +990,9 @@ int pns_operator_apply(pns_ctx* ctx, int variant, const double* x_lin, const dou
 int pns_build_precond(pns_ctx* ctx, const double* x_lin) {
   if (check_ctx(ctx) || !x_lin) return PNS_ERR_ARG;
   Ctx& C = ctx->c;
+  // the aPLMM_S build matrix is the Stokes operator, which does not depend on x_lin: a built aPLMM_S
+  // preconditioner (from pns_stokes_solve or an earlier build) is already the one asked for
+  if (C.opt.variant == PNS_APLMM_S && C.pc.built && C.pc.variant == PNS_APLMM_S) return PNS_OK;
   return build_precond(C, C.pc, C.opt.variant, x_lin);
 }
 
@@ -814,11 +1013,18 @@ int pns_stokes_solve(pns_ctx* ctx, double* x, pns_stats* st) {
   if (check_ctx(ctx) || !x) return PNS_ERR_ARG;
   Ctx& C = ctx->c;
   Precond tmp;
-  CKS(build_precond(C, tmp, PNS_APLMM_S, nullptr));
+  Precond* pc = &tmp;
+  if (C.opt.variant == PNS_APLMM_S) {
+    // the context's own preconditioner is the aPLMM_S one: build it once and keep it for Newton
+    if (!C.pc.built || C.pc.variant != PNS_APLMM_S) CKS(build_precond(C, C.pc, PNS_APLMM_S, nullptr));
+    pc = &C.pc;
+  } else {
+    CKS(build_precond(C, tmp, PNS_APLMM_S, nullptr));
+  }
   CK(cudaMemsetAsync(x, 0, sizeof(double) * C.nfull, C.stream));
   int maxn = C.opt.max_newton;
   C.opt.max_newton = std::min(maxn, 3);
-  int code = newton(C, tmp, 1, x, nullptr, st);
+  int code = newton(C, *pc, 1, x, nullptr, st);
   C.opt.max_newton = maxn;
   return code;
 }

@@ -81,6 +81,8 @@ extern "C" int pns_precond_apply_static(pns_ctx* ctx, const double* v, double* z
   Ctx& C = ctx->c;
   Precond& pc = C.pc;
   if (!pc.built) return set_err(C, PNS_ERR_STATE, "preconditioner not built");
+  if (pc.variant == PNS_BLOCK_SCHUR)
+    return set_err(C, PNS_ERR_ARG, "pns_precond_apply_static: not available for the block comparator");
   const long long n = C.nfull;
   const size_t pkel = (size_t)std::max(pc.prim.n_total, pc.dual.n_total);
   const size_t pkb = pkel * (pc.precision == PNS_FP64 ? sizeof(double) : sizeof(float));

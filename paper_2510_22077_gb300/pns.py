@@ -11,8 +11,9 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libpns.so")
 
-GPLMM, APLMM_NS, APLMM_S, ML_ONLY = 0, 1, 2, 3
-VARIANTS = {"gplmm": GPLMM, "aplmm_ns": APLMM_NS, "aplmm_s": APLMM_S, "ml_only": ML_ONLY}
+GPLMM, APLMM_NS, APLMM_S, ML_ONLY, BLOCK_SCHUR = 0, 1, 2, 3, 4
+VARIANTS = {"gplmm": GPLMM, "aplmm_ns": APLMM_NS, "aplmm_s": APLMM_S, "ml_only": ML_ONLY,
+            "block_schur": BLOCK_SCHUR}
 FP64, FP32, BF16 = 0, 1, 2
 PRECISIONS = {"fp64": FP64, "fp32": FP32, "bf16": BF16}
 COMBINE_BUILD, COMBINE_CURRENT = 0, 1
@@ -32,7 +33,8 @@ class Options(ctypes.Structure):
                 ("combine", ctypes.c_int), ("n_dilate", ctypes.c_int), ("n_tag", ctypes.c_int),
                 ("restart", ctypes.c_int), ("max_fgmres", ctypes.c_int), ("max_newton", ctypes.c_int),
                 ("inner_tol", ctypes.c_double), ("newton_tol", ctypes.c_double), ("refine_steps", ctypes.c_int),
-                ("timing", ctypes.c_int), ("stream", ctypes.c_void_p)]
+                ("timing", ctypes.c_int), ("stream", ctypes.c_void_p), ("block_inner_its", ctypes.c_int),
+                ("block_inner_tol", ctypes.c_double)]
 
 
 class Stats(ctypes.Structure):
@@ -123,7 +125,8 @@ class Solver:
 
     def __init__(self, mask, labels, rho, mu, b, dt=0.0, variant="gplmm", precision="fp64", combine="build",
                  periodic=(True, False, False), n_dilate=1, n_tag=1, restart=100, max_fgmres=2000, max_newton=30,
-                 inner_tol=1e-9, newton_tol=1e-8, timing=False, stream=None):
+                 inner_tol=1e-9, newton_tol=1e-8, timing=False, stream=None, block_inner_its=20,
+                 block_inner_tol=1e-2):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("libpns needs a CUDA device")
@@ -146,6 +149,7 @@ class Solver:
         o.max_fgmres, o.max_newton = max_fgmres, max_newton
         o.inner_tol, o.newton_tol = inner_tol, newton_tol
         o.timing = int(bool(timing))
+        o.block_inner_its, o.block_inner_tol = int(block_inner_its), float(block_inner_tol)
         s = stream if stream is not None else torch.cuda.current_stream()
         o.stream = ctypes.c_void_p(s.cuda_stream)
         self.stream = s

@@ -262,3 +262,23 @@ def test_coarse_inverse_matches_oracle_and_repeats(c1, variant):
     kept = list(range(M.n_ci)) + [M.n_ci + int(i) for i in M.coarse_prim]
     assert rel(got[0][np.ix_(kept, kept)], ref) < tol, rel(got[0][np.ix_(kept, kept)], ref)
     assert rel(got[1], got[0]) < 1e-12
+
+
+def test_aplmm_s_stokes_preconditioner_is_kept(c1):
+    """With variant aPLMM_S the Stokes solve's preconditioner is the context's own: Newton reuses it
+    (its apply equals a fresh aPLMM_S build's) and the converged solution matches the oracle."""
+    from oracle import krylov
+    mu = 3.8746364606724244
+    pb = problem(c1, mu=mu)
+    S = solver(c1, mu=mu, variant="aplmm_s", precision="fp32", newton_tol=1e-12, inner_tol=1e-12)
+    x, _ = S.pns_stokes_solve()
+    S.pns_build_precond(x)          # returns at once: the aPLMM_S build does not depend on x
+    v = to_dev(random_vector(pb, seed=4))
+    z_kept = S.pns_precond_apply(v).cpu().numpy()
+    S2 = solver(c1, mu=mu, variant="aplmm_s", precision="fp32")
+    S2.pns_build_precond(S2.zeros())
+    assert rel(z_kept, S2.pns_precond_apply(v).cpu().numpy()) < 1e-6
+    st = S.pns_newton_solve(x)
+    assert st["status"] == "PNS_OK"
+    x_ref = oracle_converged(pb, krylov.stokes_solution(pb))
+    assert rel(x.cpu().numpy(), x_ref) < 1e-8
