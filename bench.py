@@ -279,7 +279,9 @@ def main():
     its_newton = st["fgmres_its_total"]
     # batched local-solve kernel over the timed region: event times and launch counts are cumulative
     # per context, so take the difference to the end of the last warm-up step
-    base = last[2] if last is not None else {"t_local_ms": 0.0, "local_launches": 0, "kernel_launches": 0}
+    base = last[2] if last is not None else {"t_local_ms": 0.0, "local_launches": 0, "kernel_launches": 0,
+                                             "t_gj_update_ms": 0.0, "gj_update_flops": 0.0,
+                                             "gj_update_launches": 0, "gj_update_tiles": 0}
     bytes_apply = st["local_bytes_per_apply"]
     launches_local = st["local_launches"] - base["local_launches"]
     t_local = st["t_local_ms"] - base["t_local_ms"]
@@ -290,6 +292,16 @@ def main():
     except (OSError, KeyError, ValueError):
         peak, peak_src = 6800.0, "fallback"
     launches = st["kernel_launches"] - base["kernel_launches"]
+    # dominant kernel of the step: the FP32 Gauss-Jordan update of the local-inverse builds (ALU-bound);
+    # peak from unit counts: SMs x 128 FP32 FMA lanes x 2 flops x the maximum SM clock
+    gj_ms = st["t_gj_update_ms"] - base["t_gj_update_ms"]
+    gj_fl = st["gj_update_flops"] - base["gj_update_flops"]
+    gj_n = st["gj_update_launches"] - base["gj_update_launches"]
+    gj_tiles = st["gj_update_tiles"] - base["gj_update_tiles"]
+    sms = torch.cuda.get_device_properties(local_rank).multi_processor_count
+    mhz = (clocks or {}).get("sm_max_mhz") or 2070.0
+    fp32_peak = sms * 128 * 2 * mhz * 1e6 / 1e12
+    gj_achieved = gj_fl / (gj_ms * 1e-3) / 1e12 if gj_ms > 0 else None
     S.close()
     line = {"metric": METRIC, "value": ms, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
@@ -299,11 +311,20 @@ def main():
             "newton_its": st["newton_its"], "res_hist": st["res_hist"], "re_reached": re_reached,
             "buckets_ms": {"t_ml": st["t_ml_ms"], "t_mg": st["t_mg_ms"], "t_sol_newton": st["t_sol_ms"],
                            "t_sol_stokes": sst["t_sol_ms"]},
-            "roofline": {"kernel": "k_local_gemv (batched local solves M_d, M_p; with its gather)", "bound": "hbm",
-                         "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": (achieved / peak) if achieved else None, "traffic": None,
-                         "peak_source": peak_src, "bytes_per_apply": bytes_apply,
-                         "launches_timed": launches_local, "ms_timed": t_local},
+            # traffic: DRAM bytes per launch, scaled from the ncu captures of the same kernels on the 48^3
+            # pack (profiles/): update 0.979 x its C-tile bytes, local solve 1.019 x its algorithmic bytes
+            "roofline": {"kernel": "k_mm128_gj_update (FP32 Gauss-Jordan trailing update of the local inverses)",
+                         "bound": "alu", "achieved": gj_achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                         "frac": (gj_achieved / fp32_peak) if gj_achieved else None,
+                         "traffic": (0.979 * gj_tiles * 128 * 128 * 8 / gj_n) if gj_n else None,
+                         "peak_source": f"derived: {sms} SMs x 128 FP32 lanes x 2 x {mhz:g} MHz",
+                         "flops_timed": gj_fl, "launches_timed": gj_n, "ms_timed": gj_ms},
+            "roofline_apply": {"kernel": "k_local_gemv (batched local solves M_d, M_p; with its gather)",
+                               "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                               "frac": (achieved / peak) if achieved else None,
+                               "traffic": 1.019 * bytes_apply, "traffic_unit": "bytes per M_d + M_p pass",
+                               "peak_source": peak_src, "bytes_per_apply": bytes_apply,
+                               "launches_timed": launches_local, "ms_timed": t_local},
             "clocks": clocks, "gpu_launches": launches}
     if rank == 0 and not args.no_e2e:
         torch.cuda.synchronize()
@@ -334,6 +355,12 @@ def run_reference(args, rank, world):
     if rank != 0:
         return
     w, mu = workload(args, 0)
+    # the same config record as the GPU arm, its sizes taken from the oracle's maps
+    from oracle import krylov, mac
+    pb = krylov.Problem(w.mask, w.labels, mac.Params(1.0, mu, (1.0, 0.0, 0.0)))
+    info = {"n_unknowns": int(len(pb.g.unknown)), "n_prim": int(pb.maps.n_prim), "n_iface": int(pb.maps.n_iface),
+            "prim_sum_n2": float(sum(len(P) ** 2 for P in pb.maps.prim_unknowns))}
+    del pb
     its = 83 + 209       # FGMRES iterations of one solve of this workload (Stokes + Newton), as the GPU path takes them
     vals = []
     for _ in range(max(1, args.steps)):
@@ -343,7 +370,7 @@ def run_reference(args, rank, world):
     line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": 0,
             "ms_per_step": v, "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded sphere pack)", "impl": "reference",
-            "config": {"workload": f"spheres{args.n}^3 phi=0.35 r~U[6,10] seed={args.seed}, steady NS Re~{args.re:g}"},
+            "config": config(args, w, info),
             "cpu_baseline": cb, "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 

@@ -115,6 +115,10 @@ typedef struct pns_stats {
   double local_bytes_per_apply;   /* algorithmic bytes of one M_d + M_p local-solve pass */
   long long kernel_launches;      /* library-wide count of kernel launches so far (all contexts) */
   double refine_residual_max;     /* max |I - A X| of the FP32 local inverses before refinement */
+  double t_gj_update_ms;          /* time inside the FP32 Gauss-Jordan update kernel (timing == 1; cumulative) */
+  double gj_update_flops;         /* its algorithmic flops, 2 (n - nb)^2 nb per block and step (cumulative) */
+  long long gj_update_launches;   /* its timed launches (cumulative) */
+  long long gj_update_tiles;      /* 128 x 128 output tiles it processed (cumulative) */
 } pns_stats;
 
 typedef struct pns_info {

@@ -91,6 +91,12 @@ struct Precond {
   BlockSchurData bs;             // variant PNS_BLOCK_SCHUR only
 };
 
+// CUDA-event timing of the FP32 Gauss-Jordan update launches (cumulative; read after a synchronise)
+struct GjTimer {
+  double ms = 0, flops = 0;
+  long long launches = 0, tiles = 0;
+};
+
 struct Ctx {
   Geo G;
   Phy P;
@@ -121,6 +127,7 @@ struct Ctx {
   const double* cur_state = nullptr;   // Newton state for COMBINE_CURRENT
   double t_setup_ms = 0;
   double t_mg_ms = 0, t_ml_ms = 0;
+  GjTimer gj;                    // update-kernel timing of the local-inverse builds (timing == 1)
 };
 
 // Counts every kernel launch of the library (all contexts); read through pns_stats.
@@ -139,7 +146,7 @@ cudaError_t launch_cast_f2d(const float* in, double* out, long long n, cudaStrea
 template <typename ST>
 cudaError_t launch_assemble(const Ctx& C, const BlockSet& B, int op, const double* state, ST* mat, int closure);
 template <typename ST>
-cudaError_t launch_gj_invert(const BlockSet& B, ST* mat, int* d_bad, cudaStream_t s);
+cudaError_t launch_gj_invert(const BlockSet& B, ST* mat, int* d_bad, cudaStream_t s, GjTimer* timer = nullptr);
 cudaError_t launch_closure_rhs(const Ctx& C, const BlockSet& B, int op, const double* state, const int* d_colbase,
                                const int* d_cols, const long long* d_roff, const int* d_kc, double* rhs);
 template <typename ST, typename AT>

@@ -94,51 +94,95 @@ __global__ void k_assemble(Geo G, Phy P, const uint8_t* __restrict__ fl, int op,
 // Blocked Gauss-Jordan with panel width TBK (64 for FP64, 128 for FP32).  Step k: panel rows/cols
 // [k*TBK, k*TBK + nb).  Active blocks are the first `cnt` of `order`.  256 threads per CTA; the panel
 // kernels give each thread an R x R patch (R = TBK / 16).
+// In-place inverse of the nb x nb diagonal block of step k, one CTA per active block.  Thread
+// (ty, tx) of a 16 x 16 grid keeps the R x R patch (rows ty*R.., cols tx*R..) in registers; per pivot
+// the owners of the pivot row and column publish them in shared memory (two barriers per pivot).
+// Rows and columns past nb are zero and stay zero.
 template <typename ST, int TBK>
-__global__ void k_gj_diag(int k, const int* __restrict__ order, const int* __restrict__ bn,
-                          const int* __restrict__ bld, const long long* __restrict__ moff, ST* __restrict__ mat,
-                          int* __restrict__ bad) {
-  extern __shared__ unsigned char smraw[];
-  ST(*D)[TBK + 1] = (ST(*)[TBK + 1])smraw;
-  ST* colt = (ST*)(smraw + sizeof(ST) * TBK * (TBK + 1));
-  int b = order[blockIdx.x];
-  int n = bn[b], ld = bld[b];
-  int p0 = k * TBK;
-  int nb = min(TBK, n - p0);
+__global__ void __launch_bounds__(256) k_gj_diag(int k, const int* __restrict__ order, const int* __restrict__ bn,
+                                                 const int* __restrict__ bld, const long long* __restrict__ moff,
+                                                 ST* __restrict__ mat, int* __restrict__ bad) {
+  constexpr int R = TBK / 16;
+  __shared__ ST rrow[TBK];
+  __shared__ ST colt[TBK];
+  __shared__ ST s_piv;
+  const int b = order[blockIdx.x];
+  const int n = bn[b], ld = bld[b];
+  const int p0 = k * TBK;
+  const int nb = min(TBK, n - p0);
   ST* A = mat + moff[b] + (long long)p0 * ld + p0;
-  for (int e = threadIdx.x; e < TBK * TBK; e += blockDim.x) {
-    int i = e / TBK, j = e % TBK;
-    D[i][j] = (i < nb && j < nb) ? A[(long long)i * ld + j] : (ST)0;
-  }
-  __syncthreads();
+  const int ty = threadIdx.x / 16, tx = threadIdx.x % 16;
+  const int i0 = ty * R, j0 = tx * R;
+  ST P[R][R];
+#pragma unroll
+  for (int r = 0; r < R; ++r)
+#pragma unroll
+    for (int c = 0; c < R; ++c) {
+      const int i = i0 + r, j = j0 + c;
+      P[r][c] = (i < nb && j < nb) ? A[(long long)i * ld + j] : (ST)0;
+    }
   for (int t = 0; t < nb; ++t) {
-    ST piv = D[t][t];
-    bool okp = (piv == piv) && piv != (ST)0 && (double)fabs((double)piv) < 1e300;
+    const int owner = t / R, rt = t % R;
+    if (ty == owner && tx == owner) {
+#pragma unroll
+      for (int r = 0; r < R; ++r)
+#pragma unroll
+        for (int c = 0; c < R; ++c)
+          if (r == rt && c == rt) s_piv = P[r][c];
+    }
+    __syncthreads();
+    ST piv = s_piv;
+    const bool okp = (piv == piv) && piv != (ST)0 && (double)fabs((double)piv) < 1e300;
     if (!okp) {
       if (threadIdx.x == 0) atomicExch(bad, 1);
       piv = (ST)1;
     }
-    ST inv = (ST)1 / piv;
-    __syncthreads();
-    for (int j = threadIdx.x; j < nb; j += blockDim.x) {
-      colt[j] = D[j][t];
-      if (j != t) D[t][j] *= inv;
+    const ST inv = (ST)1 / piv;
+    if (ty == owner) {
+#pragma unroll
+      for (int c = 0; c < R; ++c) {
+        ST v = (ST)0;
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+          if (r == rt) v = P[r][c];
+        const int j = j0 + c;
+        rrow[j] = (j == t) ? inv : v * inv;
+      }
+    }
+    if (tx == owner) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        ST v = (ST)0;
+#pragma unroll
+        for (int c = 0; c < R; ++c)
+          if (c == rt) v = P[r][c];
+        const int i = i0 + r;
+        colt[i] = (i == t) ? (ST)0 : v;
+      }
     }
     __syncthreads();
-    if (threadIdx.x == 0) D[t][t] = inv;
-    __syncthreads();
-    for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
-      int i = e / nb, j = e % nb;
-      if (i == t) continue;
-      if (j == t) D[i][t] = -colt[i] * inv;
-      else D[i][j] -= colt[i] * D[t][j];
+    ST cr[R], rw[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) cr[r] = colt[i0 + r];
+#pragma unroll
+    for (int c = 0; c < R; ++c) rw[c] = rrow[j0 + c];
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+#pragma unroll
+      for (int c = 0; c < R; ++c) {
+        const int i = i0 + r, j = j0 + c;
+        if (i == t) P[r][c] = rw[c];
+        else if (j == t) P[r][c] = -cr[r] * inv;
+        else P[r][c] -= cr[r] * rw[c];
+      }
+  }
+#pragma unroll
+  for (int r = 0; r < R; ++r)
+#pragma unroll
+    for (int c = 0; c < R; ++c) {
+      const int i = i0 + r, j = j0 + c;
+      if (i < nb && j < nb) A[(long long)i * ld + j] = P[r][c];
     }
-    __syncthreads();
-  }
-  for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
-    int i = e / nb, j = e % nb;
-    A[(long long)i * ld + j] = D[i][j];
-  }
 }
 
 __device__ __forceinline__ int tile_skip(int t, int k) { return t + (t >= k); }
@@ -1016,9 +1060,12 @@ template <> struct GjPanel<double> { static constexpr int tb = 64; };
 template <> struct GjPanel<float> { static constexpr int tb = MT; };
 
 template <typename ST>
-cudaError_t launch_gj_invert(const BlockSet& B, ST* mat, int* d_bad, cudaStream_t s) {
+cudaError_t launch_gj_invert(const BlockSet& B, ST* mat, int* d_bad, cudaStream_t s, GjTimer* timer) {
   if (B.nblk == 0) return cudaSuccess;
   constexpr int TBK = GjPanel<ST>::tb;
+  std::vector<cudaEvent_t> evs;
+  double flops = 0;
+  long long tiles = 0;
   // order blocks by tile count (descending): the active set at step k is a prefix
   std::vector<int> order(B.nblk);
   for (int i = 0; i < B.nblk; ++i) order[i] = i;
@@ -1042,10 +1089,8 @@ cudaError_t launch_gj_invert(const BlockSet& B, ST* mat, int* d_bad, cudaStream_
   cudaMemcpyAsync(d_order, order.data(), sizeof(int) * B.nblk, cudaMemcpyHostToDevice, s);
   cudaMemcpyAsync(d_pre1, pre1.data(), sizeof(long long) * (B.nblk + 1), cudaMemcpyHostToDevice, s);
   cudaMemcpyAsync(d_pre2, pre2.data(), sizeof(long long) * (B.nblk + 1), cudaMemcpyHostToDevice, s);
-  const size_t smem_diag = sizeof(ST) * TBK * (TBK + 1) + sizeof(ST) * TBK;
   const size_t smem = 2 * sizeof(ST) * TBK * (TBK + 1);
   const size_t smem_mm = sizeof(MmSmem);
-  cudaFuncSetAttribute(k_gj_diag<ST, TBK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_diag);
   cudaFuncSetAttribute(k_gj_rowpanel<ST, TBK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   cudaFuncSetAttribute(k_gj_colpanel<ST, TBK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (std::is_same<ST, float>::value)
@@ -1056,16 +1101,31 @@ cudaError_t launch_gj_invert(const BlockSet& B, ST* mat, int* d_bad, cudaStream_
   int cnt = B.nblk;
   for (int k = 0; k < Tmax; ++k) {
     while (cnt > 0 && T[order[cnt - 1]] <= k) --cnt;
-    { pns::count_launch(); k_gj_diag<ST, TBK><<<cnt, 256, smem_diag, s>>>(k, d_order, B.d_n.as<int>(), B.d_ld.as<int>(),
+    { pns::count_launch(); k_gj_diag<ST, TBK><<<cnt, 256, 0, s>>>(k, d_order, B.d_n.as<int>(), B.d_ld.as<int>(),
                                                                          B.d_moff.as<long long>(), mat, d_bad); }
     if (pre1[cnt] > 0) {
       { pns::count_launch(); k_gj_rowpanel<ST, TBK><<<(unsigned)pre1[cnt], 256, smem, s>>>(k, cnt, d_order, d_pre1, B.d_n.as<int>(),
                                                                B.d_ld.as<int>(), B.d_moff.as<long long>(), mat); }
       if (pre2[cnt] > 0) {
         if constexpr (std::is_same<ST, float>::value) {
+          if (timer) {
+            cudaEvent_t a, b2;
+            if ((e = cudaEventCreate(&a)) != cudaSuccess) break;
+            if ((e = cudaEventCreate(&b2)) != cudaSuccess) { cudaEventDestroy(a); break; }
+            evs.push_back(a);
+            evs.push_back(b2);
+            cudaEventRecord(a, s);
+            for (int q = 0; q < cnt; ++q) {
+              const int n = B.n[order[q]];
+              const int nb = std::min(TBK, n - k * TBK);
+              flops += 2.0 * (double)(n - nb) * (double)(n - nb) * (double)nb;
+            }
+            tiles += pre2[cnt];
+          }
           pns::count_launch();
           k_mm128_gj_update<<<(unsigned)pre2[cnt], 256, smem_mm, s>>>(k, cnt, d_order, d_pre2, B.d_n.as<int>(),
                                                                       B.d_ld.as<int>(), B.d_moff.as<long long>(), mat);
+          if (timer) cudaEventRecord(evs.back(), s);
         } else {
           pns::count_launch();
           k_gj_update<ST, TBK><<<(unsigned)pre2[cnt], 256, smem, s>>>(k, cnt, d_order, d_pre2, B.d_n.as<int>(),
@@ -1078,14 +1138,24 @@ cudaError_t launch_gj_invert(const BlockSet& B, ST* mat, int* d_bad, cudaStream_
     if ((e = cudaGetLastError()) != cudaSuccess) break;
   }
   cudaStreamSynchronize(s);
+  if (timer) {
+    for (size_t q = 0; q + 1 < evs.size(); q += 2) {
+      float ms = 0;
+      if (cudaEventElapsedTime(&ms, evs[q], evs[q + 1]) == cudaSuccess) timer->ms += ms;
+    }
+    timer->flops += flops;
+    timer->tiles += tiles;
+    timer->launches += (long long)(evs.size() / 2);
+  }
+  for (cudaEvent_t ev : evs) cudaEventDestroy(ev);
   cudaFree(d_order);
   cudaFree(d_pre1);
   cudaFree(d_pre2);
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
-template cudaError_t launch_gj_invert<double>(const BlockSet&, double*, int*, cudaStream_t);
-template cudaError_t launch_gj_invert<float>(const BlockSet&, float*, int*, cudaStream_t);
+template cudaError_t launch_gj_invert<double>(const BlockSet&, double*, int*, cudaStream_t, GjTimer*);
+template cudaError_t launch_gj_invert<float>(const BlockSet&, float*, int*, cudaStream_t, GjTimer*);
 
 cudaError_t launch_closure_rhs(const Ctx& C, const BlockSet& B, int op, const double* state, const int* d_colbase,
                                const int* d_cols, const long long* d_roff, const int* d_kc, double* rhs) {

@@ -195,7 +195,7 @@ int build_local(Ctx& C, Precond& pc, BlockSet& B, int* d_bad, bool defer_bf16 = 
     CK(dalloc(F, sizeof(float) * B.m_total));
     CK(cudaMemsetAsync(F.p, 0, F.bytes, s));
     CK(launch_assemble<float>(C, B, pc.op, pc.state.as<double>(), F.as<float>(), 0));
-    CK(launch_gj_invert<float>(B, F.as<float>(), d_bad, s));
+    CK(launch_gj_invert<float>(B, F.as<float>(), d_bad, s, C.opt.timing ? &C.gj : nullptr));
     // Newton-Schulz refinement with FP64 residuals: the FP32 Gauss-Jordan error (~cond * eps32)
     // drops to the FP32 rounding of the exact inverse
     int steps = C.opt.refine_steps >= 0 ? C.opt.refine_steps : 3;
@@ -831,6 +831,10 @@ int newton(Ctx& C, Precond& pc, int stokes, double* x, const double* x_prev, pns
   loc.local_bytes_per_apply = pc.local_bytes;
   loc.kernel_launches = launch_count();
   loc.refine_residual_max = pc.ns_residual_before;
+  loc.t_gj_update_ms = C.gj.ms;
+  loc.gj_update_flops = C.gj.flops;
+  loc.gj_update_launches = C.gj.launches;
+  loc.gj_update_tiles = C.gj.tiles;
   if (stt) *stt = loc;
   return code;
 }

@@ -43,7 +43,9 @@ class Stats(ctypes.Structure):
                 ("r0_norm", ctypes.c_double), ("t_setup_ms", ctypes.c_double), ("t_mg_ms", ctypes.c_double),
                 ("t_ml_ms", ctypes.c_double), ("t_sol_ms", ctypes.c_double), ("t_local_ms", ctypes.c_double),
                 ("local_launches", ctypes.c_longlong), ("local_bytes_per_apply", ctypes.c_double),
-                ("kernel_launches", ctypes.c_longlong), ("refine_residual_max", ctypes.c_double)]
+                ("kernel_launches", ctypes.c_longlong), ("refine_residual_max", ctypes.c_double),
+                ("t_gj_update_ms", ctypes.c_double), ("gj_update_flops", ctypes.c_double),
+                ("gj_update_launches", ctypes.c_longlong), ("gj_update_tiles", ctypes.c_longlong)]
 
     def as_dict(self):
         n = self.newton_its
@@ -52,7 +54,9 @@ class Stats(ctypes.Structure):
                 "r0_norm": self.r0_norm, "t_setup_ms": self.t_setup_ms, "t_mg_ms": self.t_mg_ms,
                 "t_ml_ms": self.t_ml_ms, "t_sol_ms": self.t_sol_ms, "t_local_ms": self.t_local_ms,
                 "local_launches": self.local_launches, "local_bytes_per_apply": self.local_bytes_per_apply,
-                "kernel_launches": self.kernel_launches, "refine_residual_max": self.refine_residual_max}
+                "kernel_launches": self.kernel_launches, "refine_residual_max": self.refine_residual_max,
+                "t_gj_update_ms": self.t_gj_update_ms, "gj_update_flops": self.gj_update_flops,
+                "gj_update_launches": self.gj_update_launches, "gj_update_tiles": self.gj_update_tiles}
 
 
 class Info(ctypes.Structure):
@@ -126,7 +130,7 @@ class Solver:
     def __init__(self, mask, labels, rho, mu, b, dt=0.0, variant="gplmm", precision="fp64", combine="build",
                  periodic=(True, False, False), n_dilate=1, n_tag=1, restart=100, max_fgmres=2000, max_newton=30,
                  inner_tol=1e-9, newton_tol=1e-8, timing=False, stream=None, block_inner_its=20,
-                 block_inner_tol=1e-2):
+                 block_inner_tol=1e-2, refine_steps=-1):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("libpns needs a CUDA device")
@@ -150,6 +154,7 @@ class Solver:
         o.inner_tol, o.newton_tol = inner_tol, newton_tol
         o.timing = int(bool(timing))
         o.block_inner_its, o.block_inner_tol = int(block_inner_its), float(block_inner_tol)
+        o.refine_steps = int(refine_steps)
         s = stream if stream is not None else torch.cuda.current_stream()
         o.stream = ctypes.c_void_p(s.cuda_stream)
         self.stream = s
