@@ -91,9 +91,13 @@ typedef struct pns_options {
   int max_newton;        /* Newton iterations (default 30) */
   double inner_tol;      /* FGMRES: stop when ||J d + r|| < inner_tol * ||r(0)|| (default 1e-9) */
   double newton_tol;     /* Newton: stop when ||r(x)|| < newton_tol * ||r(0)|| (default 1e-8) */
-  int refine_steps;      /* Newton-Schulz steps X <- X + X (I - A X) (FP64 residual) applied to the
-                            FP32 local inverses whose max |I - A X| exceeds 1e-5, each refined while its residual keeps falling fast;
-                            -1 = automatic (up to 3 for FP32/BF16; FP64 inverts in FP64) */
+  int refine_steps;      /* accuracy of the FP32/BF16 local solves (FP64 needs none):
+                            -1 (default) one step of iterative refinement inside every local solve,
+                               z = X t, z += X (t - A_b z) with an FP64 residual from the stencil
+                               (a second pass over X per apply; error of order eps^2);
+                             0 none (the Gauss-Jordan inverse as computed);
+                             k > 0 k Newton-Schulz steps X <- X + X (I - A X) at build time on the
+                               blocks whose max |I - A X| exceeds 1e-5 (2 n^3 flops per block and step) */
   int timing;            /* 1: record CUDA events around the local-solve kernels (pns_stats) */
   void* stream;          /* cudaStream_t to enqueue on (NULL = legacy default stream) */
   int block_inner_its;   /* PNS_BLOCK_SCHUR: inner GMRES iterations per solve with F or L (default 20) */

@@ -89,6 +89,7 @@ struct Precond {
   double local_bytes = 0;        // algorithmic bytes of one M_d + M_p pass
   double ns_residual_before = 0; // max |I - A X| of the local inverses before refinement
   BlockSchurData bs;             // variant PNS_BLOCK_SCHUR only
+  bool apply_refine = false;     // one step of iterative refinement inside each local solve
 };
 
 // CUDA-event timing of the FP32 Gauss-Jordan update launches (cumulative; read after a synchronise)
@@ -112,6 +113,7 @@ struct Ctx {
   // scratch vectors (precision-dependent types; FP64 buffers sized nfull)
   DevBuf w0, w1, w2, w3, w4;     // preconditioner internals (VT)
   DevBuf pk_x, pk_y;             // packed local vectors (VT), sized max(prim, dual) n_total
+  DevBuf zpk;                    // packed FP64 local solutions of the refined local solves
   DevBuf coarse_rhs, coarse_x;   // double, n_o
   DevBuf red;                    // reduction scratch (double)
   // Krylov workspace
@@ -152,6 +154,9 @@ cudaError_t launch_closure_rhs(const Ctx& C, const BlockSet& B, int op, const do
 template <typename ST, typename AT>
 cudaError_t launch_block_mm(const BlockSet& B, const ST* mat, const double* rhs, const long long* d_roff,
                             const int* d_kc, double* out, cudaStream_t s);
+template <typename ST, typename PT>
+cudaError_t launch_local_solve_refined(const Ctx& C, const BlockSet& B, int op, const double* state, const ST* mat,
+                                       const double* t, double* z, PT* pk_x, double* zp, int add, cudaStream_t s);
 template <typename ST, typename PT>
 cudaError_t launch_local_solve(const BlockSet& B, const ST* mat, const double* t, double* z, PT* pk_x, int add,
                                cudaStream_t s);

@@ -618,14 +618,15 @@ __device__ __forceinline__ float dot16(const __nv_bfloat16* a, const float* x) {
 }
 template <typename ST> struct VecW { static constexpr int n = 16 / sizeof(ST); };
 
-// One warp per row; item = (block, first row, rows).  z[idx[row]] = y (add: atomicAdd), z in FP64.
+// One warp per row; item = (block, first row, rows).  Output (FP64) by `mode`: 0 z[idx[row]] = y,
+// 1 z[idx[row]] += y (atomic: overlapping dual grids), 2 packed zp[row] = y, 3 packed zp[row] += y.
 // The dot products run in the packed type PT (FP32 for the FP32/BF16 inverses): per-lane partial
 // sums over n/32 terms, the 32 lane partials are added in FP64.
 template <typename ST, typename PT>
 __global__ void __launch_bounds__(256) k_local_gemv(const int4* __restrict__ items, const int* __restrict__ idx,
                                                     const long long* __restrict__ ioff, const int* __restrict__ bld,
                                                     const long long* __restrict__ moff, const ST* __restrict__ mat,
-                                                    const PT* __restrict__ pk, double* __restrict__ z, int add) {
+                                                    const PT* __restrict__ pk, double* __restrict__ z, int mode) {
   int4 it = items[blockIdx.x];
   int b = it.x;
   int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -640,11 +641,55 @@ __global__ void __launch_bounds__(256) k_local_gemv(const int4* __restrict__ ite
     double a = (double)acc;
     for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
     if (lane == 0) {
-      int g = idx[ioff[b] + r];
-      if (add) atomicAdd(z + g, a);
-      else z[g] = a;
+      const long long slot = ioff[b] + r;
+      if (mode == 0) z[idx[slot]] = a;
+      else if (mode == 1) atomicAdd(z + idx[slot], a);
+      else if (mode == 2) z[slot] = a;
+      else z[slot] += a;
     }
   }
+}
+
+// Local residual of the apply-time refinement, per packed slot of a block set:
+// out[slot] = t[g] - sum_{c in block} A_b[g, c] zp[slot(c)]  (FP64 from the exact stencil row of g;
+// padding slots get 0).  The second pass of the local GEMV then adds X * out to zp.
+template <typename PT>
+__global__ void k_local_residual(Geo G, Phy P, const uint8_t* __restrict__ fl, int op, const double* __restrict__ st,
+                                 int nblk, const long long* __restrict__ ioff, const int* __restrict__ bn,
+                                 const int* __restrict__ idx, long long n_total, const double* __restrict__ t,
+                                 const double* __restrict__ zp, PT* __restrict__ out) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= n_total) return;
+  const int b = find_block(ioff, nblk, i);
+  const int r = (int)(i - ioff[b]);
+  const int n = bn[b];
+  if (r >= n) {
+    out[i] = (PT)0;
+    return;
+  }
+  const int* bidx = idx + ioff[b];
+  const double* zb = zp + ioff[b];
+  const int g = bidx[r];
+  RowList L;
+  L.n = 0;
+  any_row<double>(G, P, fl, op, st, g, L);
+  double acc = t[g];
+  for (int k = 0; k < L.n; ++k) {
+    int lc = lower_idx(bidx, n, L.col[k]);
+    if (lc < n && bidx[lc] == L.col[k]) acc -= L.val[k] * zb[lc];
+  }
+  out[i] = (PT)acc;
+}
+
+// z[idx[slot]] = zp[slot] (add: atomicAdd) for the real slots of a block set
+__global__ void k_scatter_packed(const int* __restrict__ idx, long long n_total, const double* __restrict__ zp,
+                                 double* __restrict__ z, int add) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= n_total) return;
+  const int g = idx[i];
+  if (g < 0) return;
+  if (add) atomicAdd(z + g, zp[i]);
+  else z[g] = zp[i];
 }
 
 // ------------------------------------------------------------------------------ refinement
@@ -1193,9 +1238,37 @@ cudaError_t launch_local_solve(const BlockSet& B, const ST* mat, const double* t
   long long blk = (B.n_total + thr - 1) / thr;
   { pns::count_launch(); k_gather<PT><<<(unsigned)blk, thr, 0, s>>>(B.idx.as<int>(), B.n_total, t, pk_x); }
   { pns::count_launch(); k_local_gemv<ST, PT><<<B.nitems, 256, 0, s>>>(B.items.as<int4>(), B.idx.as<int>(), B.d_ioff.as<long long>(),
-                                                B.d_ld.as<int>(), B.d_moff.as<long long>(), mat, pk_x, z, add); }
+                                                B.d_ld.as<int>(), B.d_moff.as<long long>(), mat, pk_x, z, add ? 1 : 0); }
   return cudaGetLastError();
 }
+
+// Local solve with one step of iterative refinement against the block's own matrix A_b[idx, idx]:
+// zp = X t, zp += X (t - A zp) (residual in FP64 from the stencil), then z[idx] (+)= zp.  With an
+// inverse accurate to eps this leaves an error of order eps^2, at the cost of a second pass over X.
+template <typename ST, typename PT>
+cudaError_t launch_local_solve_refined(const Ctx& C, const BlockSet& B, int op, const double* state, const ST* mat,
+                                       const double* t, double* z, PT* pk_x, double* zp, int add, cudaStream_t s) {
+  if (B.nblk == 0) return cudaSuccess;
+  int thr = 256;
+  unsigned blk = (unsigned)((B.n_total + thr - 1) / thr);
+  const int4* items = B.items.as<int4>();
+  { pns::count_launch(); k_gather<PT><<<blk, thr, 0, s>>>(B.idx.as<int>(), B.n_total, t, pk_x); }
+  { pns::count_launch(); k_local_gemv<ST, PT><<<B.nitems, 256, 0, s>>>(items, B.idx.as<int>(), B.d_ioff.as<long long>(),
+                                                B.d_ld.as<int>(), B.d_moff.as<long long>(), mat, pk_x, zp, 2); }
+  { pns::count_launch(); k_local_residual<PT><<<blk, thr, 0, s>>>(C.G, C.P, C.flags.as<uint8_t>(), op, state, B.nblk,
+                                                B.d_ioff.as<long long>(), B.d_n.as<int>(), B.idx.as<int>(), B.n_total,
+                                                t, zp, pk_x); }
+  { pns::count_launch(); k_local_gemv<ST, PT><<<B.nitems, 256, 0, s>>>(items, B.idx.as<int>(), B.d_ioff.as<long long>(),
+                                                B.d_ld.as<int>(), B.d_moff.as<long long>(), mat, pk_x, zp, 3); }
+  { pns::count_launch(); k_scatter_packed<<<blk, thr, 0, s>>>(B.idx.as<int>(), B.n_total, zp, z, add); }
+  return cudaGetLastError();
+}
+template cudaError_t launch_local_solve_refined<float, float>(const Ctx&, const BlockSet&, int, const double*,
+                                                              const float*, const double*, double*, float*, double*,
+                                                              int, cudaStream_t);
+template cudaError_t launch_local_solve_refined<__nv_bfloat16, float>(const Ctx&, const BlockSet&, int, const double*,
+                                                                      const __nv_bfloat16*, const double*, double*,
+                                                                      float*, double*, int, cudaStream_t);
 template cudaError_t launch_local_solve<double, double>(const BlockSet&, const double*, const double*, double*,
                                                         double*, int, cudaStream_t);
 template cudaError_t launch_local_solve<float, float>(const BlockSet&, const float*, const double*, double*, float*,

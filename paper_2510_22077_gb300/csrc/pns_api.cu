@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <type_traits>
 
 #include "internal.h"
 
@@ -196,9 +197,11 @@ int build_local(Ctx& C, Precond& pc, BlockSet& B, int* d_bad, bool defer_bf16 = 
     CK(cudaMemsetAsync(F.p, 0, F.bytes, s));
     CK(launch_assemble<float>(C, B, pc.op, pc.state.as<double>(), F.as<float>(), 0));
     CK(launch_gj_invert<float>(B, F.as<float>(), d_bad, s, C.opt.timing ? &C.gj : nullptr));
-    // Newton-Schulz refinement with FP64 residuals: the FP32 Gauss-Jordan error (~cond * eps32)
-    // drops to the FP32 rounding of the exact inverse
-    int steps = C.opt.refine_steps >= 0 ? C.opt.refine_steps : 3;
+    // Newton-Schulz refinement with FP64 residuals (refine_steps > 0): the FP32 Gauss-Jordan error
+    // (~cond * eps32) drops to the FP32 rounding of the exact inverse.  By default the refinement is
+    // done in the apply instead (one step of iterative refinement per local solve, pc.apply_refine),
+    // which costs a second pass over X per apply rather than a 2 n^3 product per block and build.
+    int steps = C.opt.refine_steps > 0 ? C.opt.refine_steps : 0;
     if (steps > 0) {
       size_t fr = 0, tot = 0;
       cudaMemGetInfo(&fr, &tot);
@@ -357,6 +360,10 @@ int ensure_scratch(Ctx& C, const Precond& pc) {
   long long pk = std::max(pc.prim.n_total, pc.dual.n_total);
   size_t pb = (size_t)vt_bytes(precision) * std::max(1LL, pk);
   if (C.pk_x.bytes < pb) CK(dalloc(C.pk_x, pb));
+  if (pc.apply_refine) {
+    size_t zb = sizeof(double) * std::max(1LL, pk);
+    if (C.zpk.bytes < zb) CK(dalloc(C.zpk, zb));
+  }
   size_t cb = sizeof(double) * std::max(1, pc.n_o);
   if (C.coarse_rhs.bytes < cb) CK(dalloc(C.coarse_rhs, cb));
   if (C.coarse_x.bytes < cb) CK(dalloc(C.coarse_x, cb));
@@ -555,6 +562,7 @@ int build_precond(Ctx& C, Precond& pc, int variant, const double* x_lin) {
   pc.ns_residual_before = 0;
   pc.variant = variant;
   pc.precision = C.opt.precision;
+  pc.apply_refine = pc.precision != PNS_FP64 && C.opt.refine_steps < 0;
   pc.op = op_of_variant(variant);
   pc.coarse = variant != PNS_ML_ONLY;
   pc.n_cif = (int)C.M.coarse_ifaces.size();
@@ -592,8 +600,8 @@ int build_precond(Ctx& C, Precond& pc, int variant, const double* x_lin) {
   pc.local_bytes = 0;
   for (BlockSet* B : {&pc.prim, &pc.dual})
     for (int b = 0; b < B->nblk; ++b)
-      pc.local_bytes += (double)B->n[b] * B->ld[b] * st_bytes(pc.precision) +   // inverse
-                        8.0 * B->n[b] + 8.0 * B->n[b] + 4.0 * B->n[b];              // t gather, z write, index
+      pc.local_bytes += (pc.apply_refine ? 2.0 : 1.0) * B->n[b] * B->ld[b] * st_bytes(pc.precision) +  // inverse
+                        (pc.apply_refine ? 60.0 : 20.0) * B->n[b];   // t, z, index (and the refinement vectors)
   CKS(ensure_scratch(C, pc));
   pc.built = true;
   return PNS_OK;
@@ -601,7 +609,6 @@ int build_precond(Ctx& C, Precond& pc, int variant, const double* x_lin) {
 
 template <typename ST, typename PT>
 int local_solve(Ctx& C, Precond& pc, BlockSet& B, const double* t, double* z, int add) {
-  (void)pc;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (C.opt.timing) {
     if (C.ev_used + 2 > C.ev_pool.size()) {
@@ -616,7 +623,16 @@ int local_solve(Ctx& C, Precond& pc, BlockSet& B, const double* t, double* z, in
     C.ev_used += 2;
     CK(cudaEventRecord(e0, C.stream));
   }
-  CK((launch_local_solve<ST, PT>(B, B.mat.as<ST>(), t, z, C.pk_x.as<PT>(), add, C.stream)));
+  if constexpr (!std::is_same<ST, double>::value) {
+    if (pc.apply_refine) {
+      CK((launch_local_solve_refined<ST, PT>(C, B, pc.op, pc.state.as<double>(), B.mat.as<ST>(), t, z,
+                                             C.pk_x.as<PT>(), C.zpk.as<double>(), add, C.stream)));
+    } else {
+      CK((launch_local_solve<ST, PT>(B, B.mat.as<ST>(), t, z, C.pk_x.as<PT>(), add, C.stream)));
+    }
+  } else {
+    CK((launch_local_solve<ST, PT>(B, B.mat.as<ST>(), t, z, C.pk_x.as<PT>(), add, C.stream)));
+  }
   if (C.opt.timing) {
     CK(cudaEventRecord(e1, C.stream));
     C.local_launches += 1;

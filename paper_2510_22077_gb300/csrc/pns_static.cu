@@ -87,7 +87,8 @@ extern "C" int pns_precond_apply_static(pns_ctx* ctx, const double* v, double* z
   const size_t pkel = (size_t)std::max(pc.prim.n_total, pc.dual.n_total);
   const size_t pkb = pkel * (pc.precision == PNS_FP64 ? sizeof(double) : sizeof(float));
   const size_t vb = align256(sizeof(double) * (size_t)n);
-  const size_t need = 5 * vb + align256(pkb) + 2 * align256(sizeof(double) * (size_t)std::max(1, pc.n_o));
+  const size_t zpb = pc.apply_refine ? align256(sizeof(double) * std::max<size_t>(1, pkel)) : 0;
+  const size_t need = 5 * vb + align256(pkb) + zpb + 2 * align256(sizeof(double) * (size_t)std::max(1, pc.n_o));
   if (need > STATIC_SCRATCH_BYTES) {
     char msg[200];
     snprintf(msg, sizeof msg, "pns_precond_apply_static: problem needs %zu bytes of scratch, the static array has %zu",
@@ -104,7 +105,8 @@ extern "C" int pns_precond_apply_static(pns_ctx* ctx, const double* v, double* z
   double* zp = (double*)p; p += vb;
   void* pk = p; p += align256(pkb);
   double* crhs = (double*)p; p += align256(sizeof(double) * (size_t)std::max(1, pc.n_o));
-  double* cx = (double*)p;
+  double* cx = (double*)p; p += align256(sizeof(double) * (size_t)std::max(1, pc.n_o));
+  double* zpk = (double*)p;
   const cudaStream_t s = C.stream;
   int op = pc.op;
   const double* st = pc.state.as<double>();
@@ -124,16 +126,28 @@ extern "C" int pns_precond_apply_static(pns_ctx* ctx, const double* v, double* z
   CKT(cudaMemsetAsync(zd, 0, sizeof(double) * n, s));
   if (pc.precision == PNS_FP64)
     CKT((launch_local_solve<double, double>(pc.dual, pc.dual.mat.as<double>(), t1, zd, (double*)pk, 1, s)));
+  else if (pc.precision == PNS_FP32 && pc.apply_refine)
+    CKT((launch_local_solve_refined<float, float>(C, pc.dual, pc.op, pc.state.as<double>(), pc.dual.mat.as<float>(),
+                                                  t1, zd, (float*)pk, zpk, 1, s)));
   else if (pc.precision == PNS_FP32)
     CKT((launch_local_solve<float, float>(pc.dual, pc.dual.mat.as<float>(), t1, zd, (float*)pk, 1, s)));
+  else if (pc.apply_refine)
+    CKT((launch_local_solve_refined<__nv_bfloat16, float>(C, pc.dual, pc.op, pc.state.as<double>(),
+                                                          pc.dual.mat.as<__nv_bfloat16>(), t1, zd, (float*)pk, zpk, 1, s)));
   else
     CKT((launch_local_solve<__nv_bfloat16, float>(pc.dual, pc.dual.mat.as<__nv_bfloat16>(), t1, zd, (float*)pk, 1, s)));
   CKT(launch_apply<double>(C, op, st, zd, t1, t2, true));
   CKT(cudaMemsetAsync(zp, 0, sizeof(double) * n, s));
   if (pc.precision == PNS_FP64)
     CKT((launch_local_solve<double, double>(pc.prim, pc.prim.mat.as<double>(), t2, zp, (double*)pk, 0, s)));
+  else if (pc.precision == PNS_FP32 && pc.apply_refine)
+    CKT((launch_local_solve_refined<float, float>(C, pc.prim, pc.op, pc.state.as<double>(), pc.prim.mat.as<float>(),
+                                                  t2, zp, (float*)pk, zpk, 0, s)));
   else if (pc.precision == PNS_FP32)
     CKT((launch_local_solve<float, float>(pc.prim, pc.prim.mat.as<float>(), t2, zp, (float*)pk, 0, s)));
+  else if (pc.apply_refine)
+    CKT((launch_local_solve_refined<__nv_bfloat16, float>(C, pc.prim, pc.op, pc.state.as<double>(),
+                                                          pc.prim.mat.as<__nv_bfloat16>(), t2, zp, (float*)pk, zpk, 0, s)));
   else
     CKT((launch_local_solve<__nv_bfloat16, float>(pc.prim, pc.prim.mat.as<__nv_bfloat16>(), t2, zp, (float*)pk, 0, s)));
   { pns::count_launch(); k_sum3_static<<<2048, 256, 0, s>>>(zG, zd, zp, z, n); }

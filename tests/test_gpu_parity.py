@@ -282,3 +282,19 @@ def test_aplmm_s_stokes_preconditioner_is_kept(c1):
     assert st["status"] == "PNS_OK"
     x_ref = oracle_converged(pb, krylov.stokes_solution(pb))
     assert rel(x.cpu().numpy(), x_ref) < 1e-8
+
+
+@pytest.mark.parametrize("refine_steps", [-1, 2])
+def test_fp32_refinement_modes_meet_the_bar(c1, refine_steps):
+    """FP32 local inverses refined either inside each local solve (default, -1) or by Newton-Schulz
+    steps at build time (2): both applies match the FP64 oracle to 1e-5."""
+    pb = problem(c1, mu=3.87)
+    x = random_state(pb, seed=2, scale=0.1)
+    M, A_b = pb.preconditioner("gplmm", x)
+    v = random_vector(pb, seed=3)
+    z_o = M.apply(v, A_b)
+    S = solver(c1, mu=3.87, variant="gplmm", precision="fp32", refine_steps=refine_steps)
+    S.pns_build_precond(to_dev(x))
+    err = rel(S.pns_precond_apply(to_dev(v)).cpu().numpy(), z_o)
+    print(f"fp32 apply, refine_steps {refine_steps}: rel err {err:.2e}")
+    assert err < 1e-5, err
