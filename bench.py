@@ -45,9 +45,9 @@ def parse():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--compare", default="",
-                    help="comma-separated preconditioner variants to time once each after the main run "
-                         "(e.g. gplmm,aplmm_ns,aplmm_s,block_schur); results go to the 'variants' key")
+    ap.add_argument("--compare", default="aplmm_s,block_schur",
+                    help="comma-separated preconditioner variants to time once each after the main run at N=1 "
+                         "(results under 'variants'; 'none' to skip)")
     return ap.parse_args()
 
 
@@ -340,7 +340,7 @@ def main():
         S2.close()
         line["e2e"] = {"value": e2e_ms, "unit": UNIT, "h2d_bytes_per_step": int(w.mask.nbytes + w.labels.nbytes),
                        "d2h_bytes_per_step": int(host.nbytes)}
-    if rank == 0 and args.compare:
+    if rank == 0 and world == 1 and args.compare and args.compare != "none":
         line["variants"] = compare_variants(args, w, mu)
     if rank == 0 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(w, mu, its_stokes + its_newton)
