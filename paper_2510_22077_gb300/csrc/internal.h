@@ -148,7 +148,8 @@ cudaError_t launch_cast_f2d(const float* in, double* out, long long n, cudaStrea
 template <typename ST>
 cudaError_t launch_assemble(const Ctx& C, const BlockSet& B, int op, const double* state, ST* mat, int closure);
 template <typename ST>
-cudaError_t launch_gj_invert(const BlockSet& B, ST* mat, int* d_bad, cudaStream_t s, GjTimer* timer = nullptr);
+cudaError_t launch_gj_invert(const BlockSet& B, ST* mat, int* d_bad, cudaStream_t s, GjTimer* timer = nullptr,
+                             int tensor_cores = 0);
 cudaError_t launch_closure_rhs(const Ctx& C, const BlockSet& B, int op, const double* state, const int* d_colbase,
                                const int* d_cols, const long long* d_roff, const int* d_kc, double* rhs);
 template <typename ST, typename AT>

@@ -426,6 +426,162 @@ __device__ __forceinline__ void mm128_mainloop(const float* __restrict__ A, long
   }
 }
 
+// Same staging as mm128_mainloop, product on the tensor cores: mma.sync m16n8k8 TF32 with FP32
+// accumulation, each operand split as x = hi + lo (hi = x rounded to TF32, lo = the remainder rounded
+// to TF32) and acc += hi*hi + hi*lo + lo*hi, which keeps the product close to FP32 accuracy.  Warp w
+// owns the 64 x 32 sub-tile at rows 64*(w/4), columns 32*(w%4): 4 x 4 MMA tiles of 16 x 8.
+// Fragment layout of m16n8k8 (g = lane/4, t = lane%4): A rows g, g+8 and k t, t+4; B k t, t+4 and
+// column g; C rows g, g+8 and columns 2t, 2t+1.
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;\n" : "=r"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ void split_tf32(float x, uint32_t& hi, uint32_t& lo) {
+  hi = to_tf32(x);
+  lo = to_tf32(x - __uint_as_float(hi));
+}
+__device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+__device__ __forceinline__ void mm128_mainloop_tc(const float* __restrict__ A, long long lda, int rows_ok,
+                                                  const float* __restrict__ B, long long ldb, int cols_ok, int K,
+                                                  int a_cols_ok, float acc[4][4][4], MmSmem& sm) {
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5, lane = tid & 31;
+  const int g = lane >> 2, t4 = lane & 3;
+  const int wm = (warp >> 2) * 64, wn = (warp & 3) * 32;
+  float4 ra[4];
+  auto fetch = [&](int c0, int st) {
+#pragma unroll
+    for (int rep = 0; rep < 4; ++rep) {
+      int q = tid + rep * 256;
+      int i = q % MT, kq = (q / MT) * 4;
+      int kg = c0 + kq;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (i < rows_ok && kg < a_cols_ok) {
+        v = *reinterpret_cast<const float4*>(A + (long long)i * lda + kg);
+        if (kg + 0 >= K) v.x = 0.f;
+        if (kg + 1 >= K) v.y = 0.f;
+        if (kg + 2 >= K) v.z = 0.f;
+        if (kg + 3 >= K) v.w = 0.f;
+      }
+      ra[rep] = v;
+      int kk = q / 32, c = (q % 32) * 4;
+      bool ok = (c0 + kk < K) && (c < cols_ok);
+      const float* src = ok ? B + (long long)(c0 + kk) * ldb + c : B;
+      cp_async16(&sm.b[st][kk][c], src, ok ? 16 : 0);
+    }
+    cp_async_commit();
+  };
+  auto stash = [&](int st) {
+#pragma unroll
+    for (int rep = 0; rep < 4; ++rep) {
+      int q = tid + rep * 256;
+      int i = q % MT, kq = (q / MT) * 4;
+      sm.a[st][kq + 0][i] = ra[rep].x;
+      sm.a[st][kq + 1][i] = ra[rep].y;
+      sm.a[st][kq + 2][i] = ra[rep].z;
+      sm.a[st][kq + 3][i] = ra[rep].w;
+    }
+  };
+  const int nchunk = (K + KC - 1) / KC;
+  fetch(0, 0);
+  stash(0);
+  cp_async_wait_all();
+  __syncthreads();
+  for (int ch = 0; ch < nchunk; ++ch) {
+    const int st = ch & 1;
+    if (ch + 1 < nchunk) fetch((ch + 1) * KC, st ^ 1);
+#pragma unroll
+    for (int k8 = 0; k8 < KC; k8 += 8) {
+      uint32_t bh[4][2], bl[4][2];
+#pragma unroll
+      for (int ni = 0; ni < 4; ++ni) {
+        const int col = wn + ni * 8 + g;
+        split_tf32(sm.b[st][k8 + t4][col], bh[ni][0], bl[ni][0]);
+        split_tf32(sm.b[st][k8 + t4 + 4][col], bh[ni][1], bl[ni][1]);
+      }
+#pragma unroll
+      for (int mi = 0; mi < 4; ++mi) {
+        const int row = wm + mi * 16 + g;
+        uint32_t ah[4], al[4];
+        split_tf32(sm.a[st][k8 + t4][row], ah[0], al[0]);
+        split_tf32(sm.a[st][k8 + t4][row + 8], ah[1], al[1]);
+        split_tf32(sm.a[st][k8 + t4 + 4][row], ah[2], al[2]);
+        split_tf32(sm.a[st][k8 + t4 + 4][row + 8], ah[3], al[3]);
+#pragma unroll
+        for (int ni = 0; ni < 4; ++ni) {
+          mma_tf32(acc[mi][ni], al, bh[ni]);
+          mma_tf32(acc[mi][ni], ah, bl[ni]);
+          mma_tf32(acc[mi][ni], ah, bh[ni]);
+        }
+      }
+    }
+    if (ch + 1 < nchunk) {
+      stash(st ^ 1);
+      cp_async_wait_all();
+    }
+    __syncthreads();
+  }
+}
+
+// Gauss-Jordan trailing update on the tensor cores (3-term TF32 split); same tiles as
+// k_mm128_gj_update.
+__global__ void __launch_bounds__(256, 2) k_mm128_gj_update_tc(int k, int cnt, const int* __restrict__ order,
+                                                               const long long* __restrict__ pre2,
+                                                               const int* __restrict__ bn, const int* __restrict__ bld,
+                                                               const long long* __restrict__ moff,
+                                                               float* __restrict__ mat) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  MmSmem& sm = *reinterpret_cast<MmSmem*>(smraw);
+  long long w = blockIdx.x;
+  int s = find_block(pre2, cnt, w);
+  int b = order[s];
+  int n = bn[b], ld = bld[b];
+  int T = (n + MT - 1) / MT;
+  long long loc = w - pre2[s];
+  int it = tile_skip((int)(loc / (T - 1)), k), jt = tile_skip((int)(loc % (T - 1)), k);
+  int p0 = k * MT, i0 = it * MT, j0 = jt * MT;
+  int nb = min(MT, n - p0);
+  int rows_ok = min(MT, ld - i0), cols_ok = min(MT, ld - j0);
+  float* Ab = mat + moff[b];
+  float acc[4][4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) acc[a][c][e] = 0.f;
+  mm128_mainloop_tc(Ab + (long long)i0 * ld + p0, ld, rows_ok, Ab + (long long)p0 * ld + j0, ld, cols_ok, nb,
+                    ld - p0, acc, sm);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int g = lane >> 2, t4 = lane & 3;
+  const int wm = (warp >> 2) * 64, wn = (warp & 3) * 32;
+#pragma unroll
+  for (int mi = 0; mi < 4; ++mi)
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int r = wm + mi * 16 + g + h * 8;
+      if (r >= rows_ok) continue;
+#pragma unroll
+      for (int ni = 0; ni < 4; ++ni) {
+        const int c = wn + ni * 8 + 2 * t4;
+        if (c >= cols_ok) continue;
+        float2* q = reinterpret_cast<float2*>(Ab + (long long)(i0 + r) * ld + j0 + c);
+        float2 v = *q;
+        v.x -= acc[mi][ni][2 * h + 0];
+        v.y -= acc[mi][ni][2 * h + 1];
+        *q = v;
+      }
+    }
+}
+
 __device__ __forceinline__ int mm_row(int ty, int i) { return (i < 4) ? ty * 4 + i : 64 + ty * 4 + (i - 4); }
 
 // Gauss-Jordan trailing update, FP32, panel width 128: A[I, J] -= A[I, P] * A[P, J] for I, J != k.
@@ -1105,7 +1261,7 @@ template <> struct GjPanel<double> { static constexpr int tb = 64; };
 template <> struct GjPanel<float> { static constexpr int tb = MT; };
 
 template <typename ST>
-cudaError_t launch_gj_invert(const BlockSet& B, ST* mat, int* d_bad, cudaStream_t s, GjTimer* timer) {
+cudaError_t launch_gj_invert(const BlockSet& B, ST* mat, int* d_bad, cudaStream_t s, GjTimer* timer, int tensor_cores) {
   if (B.nblk == 0) return cudaSuccess;
   constexpr int TBK = GjPanel<ST>::tb;
   std::vector<cudaEvent_t> evs;
@@ -1138,8 +1294,10 @@ cudaError_t launch_gj_invert(const BlockSet& B, ST* mat, int* d_bad, cudaStream_
   const size_t smem_mm = sizeof(MmSmem);
   cudaFuncSetAttribute(k_gj_rowpanel<ST, TBK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   cudaFuncSetAttribute(k_gj_colpanel<ST, TBK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (std::is_same<ST, float>::value)
+  if (std::is_same<ST, float>::value) {
     cudaFuncSetAttribute(k_mm128_gj_update, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_mm);
+    cudaFuncSetAttribute(k_mm128_gj_update_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_mm);
+  }
   else
     cudaFuncSetAttribute(k_gj_update<ST, TBK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int Tmax = T[order[0]];
@@ -1168,8 +1326,13 @@ cudaError_t launch_gj_invert(const BlockSet& B, ST* mat, int* d_bad, cudaStream_
             tiles += pre2[cnt];
           }
           pns::count_launch();
-          k_mm128_gj_update<<<(unsigned)pre2[cnt], 256, smem_mm, s>>>(k, cnt, d_order, d_pre2, B.d_n.as<int>(),
-                                                                      B.d_ld.as<int>(), B.d_moff.as<long long>(), mat);
+          if (tensor_cores)
+            k_mm128_gj_update_tc<<<(unsigned)pre2[cnt], 256, smem_mm, s>>>(k, cnt, d_order, d_pre2, B.d_n.as<int>(),
+                                                                           B.d_ld.as<int>(), B.d_moff.as<long long>(),
+                                                                           mat);
+          else
+            k_mm128_gj_update<<<(unsigned)pre2[cnt], 256, smem_mm, s>>>(k, cnt, d_order, d_pre2, B.d_n.as<int>(),
+                                                                        B.d_ld.as<int>(), B.d_moff.as<long long>(), mat);
           if (timer) cudaEventRecord(evs.back(), s);
         } else {
           pns::count_launch();
@@ -1199,8 +1362,8 @@ cudaError_t launch_gj_invert(const BlockSet& B, ST* mat, int* d_bad, cudaStream_
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
-template cudaError_t launch_gj_invert<double>(const BlockSet&, double*, int*, cudaStream_t, GjTimer*);
-template cudaError_t launch_gj_invert<float>(const BlockSet&, float*, int*, cudaStream_t, GjTimer*);
+template cudaError_t launch_gj_invert<double>(const BlockSet&, double*, int*, cudaStream_t, GjTimer*, int);
+template cudaError_t launch_gj_invert<float>(const BlockSet&, float*, int*, cudaStream_t, GjTimer*, int);
 
 cudaError_t launch_closure_rhs(const Ctx& C, const BlockSet& B, int op, const double* state, const int* d_colbase,
                                const int* d_cols, const long long* d_roff, const int* d_kc, double* rhs) {

@@ -196,7 +196,7 @@ int build_local(Ctx& C, Precond& pc, BlockSet& B, int* d_bad, bool defer_bf16 = 
     CK(dalloc(F, sizeof(float) * B.m_total));
     CK(cudaMemsetAsync(F.p, 0, F.bytes, s));
     CK(launch_assemble<float>(C, B, pc.op, pc.state.as<double>(), F.as<float>(), 0));
-    CK(launch_gj_invert<float>(B, F.as<float>(), d_bad, s, C.opt.timing ? &C.gj : nullptr));
+    CK(launch_gj_invert<float>(B, F.as<float>(), d_bad, s, C.opt.timing ? &C.gj : nullptr, C.opt.gj_tensor_cores));
     // Newton-Schulz refinement with FP64 residuals (refine_steps > 0): the FP32 Gauss-Jordan error
     // (~cond * eps32) drops to the FP32 rounding of the exact inverse.  By default the refinement is
     // done in the apply instead (one step of iterative refinement per local solve, pc.apply_refine),
@@ -404,12 +404,12 @@ int build_block_t(Ctx& C, Precond& pc, int* d_bad) {
   if (S.bf.nblk) {
     CK(dalloc(S.bf.mat, sizeof(ST) * S.bf.m_total));
     CK(launch_assemble<ST>(C, S.bf, OP_NEWTON, pc.state.as<double>(), S.bf.mat.as<ST>(), 0));
-    CK(launch_gj_invert<ST>(S.bf, S.bf.mat.as<ST>(), d_bad, s));
+    CK(launch_gj_invert<ST>(S.bf, S.bf.mat.as<ST>(), d_bad, s, nullptr, C.opt.gj_tensor_cores));
   }
   if (S.bl.nblk) {
     CK(dalloc(S.bl.mat, sizeof(ST) * S.bl.m_total));
     CK(launch_assemble_L<ST>(C, S.bl, S.D.as<double>(), S.bl.mat.as<ST>()));
-    CK(launch_gj_invert<ST>(S.bl, S.bl.mat.as<ST>(), d_bad, s));
+    CK(launch_gj_invert<ST>(S.bl, S.bl.mat.as<ST>(), d_bad, s, nullptr, C.opt.gj_tensor_cores));
   }
   S.its = C.opt.block_inner_its;
   S.tol = C.opt.block_inner_tol;
@@ -881,6 +881,7 @@ void pns_default_options(pns_options* o) {
   o->stream = nullptr;
   o->block_inner_its = 20;
   o->block_inner_tol = 1e-2;
+  o->gj_tensor_cores = 0;
 }
 
 int pns_setup(pns_ctx** out, int nz, int ny, int nx, const uint8_t* mask, const int32_t* labels, double rho,

@@ -34,7 +34,7 @@ class Options(ctypes.Structure):
                 ("restart", ctypes.c_int), ("max_fgmres", ctypes.c_int), ("max_newton", ctypes.c_int),
                 ("inner_tol", ctypes.c_double), ("newton_tol", ctypes.c_double), ("refine_steps", ctypes.c_int),
                 ("timing", ctypes.c_int), ("stream", ctypes.c_void_p), ("block_inner_its", ctypes.c_int),
-                ("block_inner_tol", ctypes.c_double)]
+                ("block_inner_tol", ctypes.c_double), ("gj_tensor_cores", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -130,7 +130,7 @@ class Solver:
     def __init__(self, mask, labels, rho, mu, b, dt=0.0, variant="gplmm", precision="fp64", combine="build",
                  periodic=(True, False, False), n_dilate=1, n_tag=1, restart=100, max_fgmres=2000, max_newton=30,
                  inner_tol=1e-9, newton_tol=1e-8, timing=False, stream=None, block_inner_its=20,
-                 block_inner_tol=1e-2, refine_steps=-1):
+                 block_inner_tol=1e-2, refine_steps=-1, gj_tensor_cores=None):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("libpns needs a CUDA device")
@@ -155,6 +155,8 @@ class Solver:
         o.timing = int(bool(timing))
         o.block_inner_its, o.block_inner_tol = int(block_inner_its), float(block_inner_tol)
         o.refine_steps = int(refine_steps)
+        if gj_tensor_cores is not None:
+            o.gj_tensor_cores = int(bool(gj_tensor_cores))
         s = stream if stream is not None else torch.cuda.current_stream()
         o.stream = ctypes.c_void_p(s.cuda_stream)
         self.stream = s
