@@ -32,7 +32,17 @@ METRIC = "time to 1e-8 Newton residual"
 UNIT = "ms"
 
 
-def parse():
+def max_over_ranks(value, dist):
+    """The maximum of a per-rank float over all ranks (a CPU tensor through the process group)."""
+    if dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=1)
@@ -48,7 +58,7 @@ def parse():
     ap.add_argument("--compare", default="aplmm_s,block_schur",
                     help="comma-separated preconditioner variants to time once each after the main run at N=1 "
                          "(results under 'variants'; 'none' to skip)")
-    return ap.parse_args()
+    return ap.parse_args(argv)
 
 
 def workload(args, rank=0):
@@ -268,9 +278,7 @@ def main():
     clocks = clk.stop()
     ms = e0.elapsed_time(e1) / args.steps
     if dist:
-        t = torch.tensor([ms], dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+        ms = max_over_ranks(ms, dist)
         dist.barrier()
     sst, st = results[-1]
     ux = x[:S.ncell].cpu().numpy().reshape(w.mask.shape)
