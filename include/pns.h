@@ -224,6 +224,19 @@ int pns_export_coarse(const pns_ctx* ctx, double* ao_inv, int* n_o);
 int pns_export_maps(const pns_ctx* ctx, int32_t* cell_prim, int32_t* cell_iface, int32_t* face_class,
                     uint8_t* tags, int32_t* dual_count, int32_t* pins);
 
+/* The same integer maps computed on the host alone, with no device and no context (Sec. 3.2.1,
+ * Sec. 3.2.2, Sec. 4; the readings of pns_setup): for checks of the index maps at any size on a
+ * machine without a GPU.
+ *   nz, ny, nx, mask, labels   as pns_setup (HOST arrays of nz*ny*nx)
+ *   periodic[3], n_dilate, n_tag   as in pns_options
+ *   outputs   as pns_export_maps, HOST arrays sized by the caller (any may be NULL); pins needs
+ *             room for nz*ny*nx entries
+ *   counts[4] (may be NULL) receives n_prim, n_iface, n_pins, n_dropped_labels.
+ * Returns PNS_ERR_ARG on bad sizes or labels inconsistent with the mask; touches no device. */
+int pns_maps_host(int nz, int ny, int nx, const uint8_t* mask, const int32_t* labels, const int periodic[3],
+                  int n_dilate, int n_tag, int32_t* cell_prim, int32_t* cell_iface, int32_t* face_class,
+                  uint8_t* tags, int32_t* dual_count, int32_t* pins, int32_t counts[4]);
+
 #ifdef __cplusplus
 }
 #endif

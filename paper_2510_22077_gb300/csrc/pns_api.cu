@@ -855,6 +855,23 @@ int newton(Ctx& C, Precond& pc, int stokes, double* x, const double* x_prev, pns
   return code;
 }
 
+void export_maps(const Maps& M, const Geo& G, int32_t* cell_prim, int32_t* cell_iface, int32_t* face_class,
+                 uint8_t* tags, int32_t* dual_count, int32_t* pins) {
+  const int nc = G.ncell, dim = G.dim;
+  if (cell_prim) std::copy(M.cell_prim.begin(), M.cell_prim.end(), cell_prim);
+  if (cell_iface) std::copy(M.cell_iface.begin(), M.cell_iface.end(), cell_iface);
+  if (face_class) std::copy(M.face_class.begin(), M.face_class.end(), face_class);
+  if (tags)
+    for (int d = 0; d < dim; ++d)
+      for (int c = 0; c < nc; ++c) tags[(size_t)d * nc + c] = (M.flags[c] & fl_tag(d)) ? 1 : 0;
+  if (dual_count) {
+    std::fill(dual_count, dual_count + (size_t)(dim + 1) * nc, 0);
+    for (auto& v : M.dual_unk)
+      for (int g : v) dual_count[g]++;
+  }
+  if (pins) std::copy(M.pins.begin(), M.pins.end(), pins);
+}
+
 int check_ctx(const pns_ctx* ctx) { return ctx ? PNS_OK : PNS_ERR_ARG; }
 
 }  // namespace
@@ -1067,19 +1084,33 @@ int pns_export_maps(const pns_ctx* ctx, int32_t* cell_prim, int32_t* cell_iface,
                     int32_t* dual_count, int32_t* pins) {
   if (check_ctx(ctx)) return PNS_ERR_ARG;
   const Ctx& C = ctx->c;
-  const int nc = C.G.ncell, dim = C.G.dim;
-  if (cell_prim) std::copy(C.M.cell_prim.begin(), C.M.cell_prim.end(), cell_prim);
-  if (cell_iface) std::copy(C.M.cell_iface.begin(), C.M.cell_iface.end(), cell_iface);
-  if (face_class) std::copy(C.M.face_class.begin(), C.M.face_class.end(), face_class);
-  if (tags)
-    for (int d = 0; d < dim; ++d)
-      for (int c = 0; c < nc; ++c) tags[(size_t)d * nc + c] = (C.M.flags[c] & fl_tag(d)) ? 1 : 0;
-  if (dual_count) {
-    std::fill(dual_count, dual_count + (size_t)(dim + 1) * nc, 0);
-    for (auto& v : C.M.dual_unk)
-      for (int g : v) dual_count[g]++;
+  export_maps(C.M, C.G, cell_prim, cell_iface, face_class, tags, dual_count, pins);
+  return PNS_OK;
+}
+
+int pns_maps_host(int nz, int ny, int nx, const uint8_t* mask, const int32_t* labels, const int periodic[3],
+                  int n_dilate, int n_tag, int32_t* cell_prim, int32_t* cell_iface, int32_t* face_class,
+                  uint8_t* tags, int32_t* dual_count, int32_t* pins, int32_t counts[4]) {
+  if (!mask || !labels || !periodic || nz < 1 || ny < 1 || nx < 1 || n_dilate < 0 || n_tag < 1) return PNS_ERR_ARG;
+  if ((long long)nx * ny * nz * 4 >= (1LL << 31)) return PNS_ERR_ARG;
+  Geo G;
+  G.nx = nx;
+  G.ny = ny;
+  G.nz = nz;
+  G.dim = nz == 1 ? 2 : 3;
+  G.ncell = nx * ny * nz;
+  for (int a = 0; a < 3; ++a) G.per[a] = periodic[a] ? 1 : 0;
+  if (G.dim == 2) G.per[2] = 0;
+  Maps M;
+  std::string err;
+  if (build_maps(G, mask, labels, n_dilate, n_tag, M, err) != 0) return PNS_ERR_ARG;
+  export_maps(M, G, cell_prim, cell_iface, face_class, tags, dual_count, pins);
+  if (counts) {
+    counts[0] = M.n_prim;
+    counts[1] = M.n_iface;
+    counts[2] = (int32_t)M.pins.size();
+    counts[3] = M.n_dropped;
   }
-  if (pins) std::copy(C.M.pins.begin(), C.M.pins.end(), pins);
   return PNS_OK;
 }
 

@@ -100,6 +100,7 @@ def load(path: str = LIB_PATH):
         "pns_stokes_solve": (I, [P, P, ctypes.POINTER(Stats)]),
         "pns_export_maps": (I, [P, P, P, P, P, P, P]),
         "pns_export_coarse": (I, [P, P, ctypes.POINTER(ctypes.c_int)]),
+        "pns_maps_host": (I, [I, I, I, P, P, P, I, I, P, P, P, P, P, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -107,6 +108,34 @@ def load(path: str = LIB_PATH):
         f.argtypes = args
     _lib = lib
     return lib
+
+
+def pns_maps_host(mask, labels, periodic=(True, False, False), n_dilate=1, n_tag=1):
+    """The integer maps of pns_setup computed by the library on the host (no device needed)."""
+    lib = load()
+    mask = np.ascontiguousarray(mask, dtype=np.uint8)
+    labels = np.ascontiguousarray(labels, dtype=np.int32)
+    if mask.ndim != 3 or labels.shape != mask.shape:
+        raise ValueError("mask and labels must be (nz, ny, nx) arrays of equal shape")
+    nz, ny, nx = mask.shape
+    dim = 2 if nz == 1 else 3
+    nc = nx * ny * nz
+    out = {"cell_prim": np.zeros(nc, np.int32), "cell_iface": np.zeros(nc, np.int32),
+           "face_class": np.zeros(dim * nc, np.int32), "tags": np.zeros(dim * nc, np.uint8),
+           "dual_count": np.zeros((dim + 1) * nc, np.int32), "pins": np.zeros(nc, np.int32)}
+    counts = np.zeros(4, np.int32)
+    per = (ctypes.c_int * 3)(*[int(bool(p)) for p in periodic])
+    P = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    rc = lib.pns_maps_host(nz, ny, nx, P(mask), P(labels), ctypes.cast(per, ctypes.c_void_p), int(n_dilate),
+                           int(n_tag), P(out["cell_prim"]), P(out["cell_iface"]), P(out["face_class"]),
+                           P(out["tags"]), P(out["dual_count"]), P(out["pins"]), P(counts))
+    if rc != 0:
+        raise PnsError(rc, "pns_maps_host: bad sizes or labels inconsistent with the mask")
+    out["face_class"] = out["face_class"].reshape(dim, nc)
+    out["tags"] = out["tags"].reshape(dim, nc).astype(bool)
+    out["pins"] = out["pins"][:counts[2]]
+    out["n_prim"], out["n_iface"], out["n_pins"], out["n_dropped_labels"] = (int(c) for c in counts)
+    return out
 
 
 def default_options() -> Options:
