@@ -46,7 +46,9 @@ __device__ __forceinline__ int lower_idx(const int* __restrict__ a, int n, int k
   return lo;
 }
 
-// small per-thread list of (column, value) with duplicates merged
+// small per-thread list of (column, value) with duplicates merged.  A stencil row has at most 17
+// distinct columns in 3D (the face itself, 6 viscous neighbours, 2 pressures, 8 advecting faces of the
+// Newton reaction term); 32 slots leave room.
 struct RowList {
   int col[32];
   double val[32];
