@@ -50,3 +50,27 @@ def test_library_loads_with_ctypes(lib_path):
     pns._lib = None
     o = pns.default_options()
     assert o.restart == 100 and o.periodic[0] == 1 and abs(o.newton_tol - 1e-8) < 1e-20
+
+
+def test_product_path_fails_loudly_without_a_device(lib_path):
+    """No CPU fallback: without a CUDA device the binding refuses to build a solver, and the C ABI's
+    pns_setup returns an error code (no context) instead of computing anything on the host."""
+    import ctypes
+
+    import numpy as np
+    import torch
+
+    from paper_2510_22077_gb300 import pns
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    mask = np.ones((1, 4, 8), np.uint8)
+    labels = np.ones((1, 4, 8), np.int32)
+    with pytest.raises(RuntimeError):
+        pns.Solver(mask, labels, 1.0, 1.0, (1.0, 0.0, 0.0))
+    lib = pns.load()
+    opt = pns.default_options()
+    ctx = ctypes.c_void_p()
+    b = (ctypes.c_double * 3)(1.0, 0.0, 0.0)
+    rc = lib.pns_setup(ctypes.byref(ctx), 1, 4, 8, mask.ctypes.data_as(ctypes.c_void_p),
+                       labels.ctypes.data_as(ctypes.c_void_p), 1.0, 1.0, b, 0.0, ctypes.byref(opt))
+    assert rc != 0 and not ctx.value
