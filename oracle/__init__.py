@@ -12,6 +12,7 @@ Modules
     plmm    -- preconditioner build and apply, recipe form and literal matrix form  (Eqs. 5-26)
     krylov  -- right-preconditioned flexible GMRES, Newton, backward-Euler stepping  (Sec. 8, Eq. 3)
     block   -- block-triangular Schur comparator with the scaled BFBt approximation  (Sec. 1, Eq. 4)
+    unet    -- 3D U-Net of the learned initial guess: NumPy forward and explicit backward, sample encoding
 
 Parity status: every function is pinned by a test in tests/test_oracle_*.py against something
 other than itself (closed forms, finite differences, brute-force dense solves, the projection
