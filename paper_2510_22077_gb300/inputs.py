@@ -306,6 +306,116 @@ def _flood(arr, amap, periodic, flat_d, seeds_lab):
     return lab
 
 
+def _touches_solid(cells, arr, amap, periodic):
+    """True when one of the flat `cells` has a face-neighbour that is solid or a non-periodic box wall."""
+    shape = arr.shape
+    wraps = {ax_np: periodic[ax_s] for ax_s, ax_np in amap.items()}
+    idx = np.array(np.unravel_index(cells, shape))
+    flat_void = arr.ravel()
+    strides = np.array([int(np.prod(shape[a + 1:])) for a in range(len(shape))])
+    for ax in range(len(shape)):
+        for sgn in (-1, 1):
+            v = idx[ax] + sgn
+            out = (v < 0) | (v >= shape[ax])
+            if not wraps[ax] and np.any(out):
+                return True
+            v = v % shape[ax]
+            nb = cells + (v - idx[ax]) * strides[ax]
+            if np.any(~flat_void[nb]):
+                return True
+    return False
+
+
+def _bisect(cells, arr, amap, periodic):
+    """Two-way split of a region with a single distance basin: cut at the median of its longest extent
+    (coordinates unwrapped around the region's first cell along periodic axes); each face-connected
+    part becomes a piece.  Returns a flat piece-label array (0 outside the region)."""
+    shape = arr.shape
+    idx = np.array(np.unravel_index(cells, shape)).astype(np.int64)
+    wraps = {ax_np: periodic[ax_s] for ax_s, ax_np in amap.items()}
+    for ax in range(len(shape)):
+        if wraps[ax]:
+            ref = idx[ax, 0]
+            d = (idx[ax] - ref + shape[ax] // 2) % shape[ax] - shape[ax] // 2
+            idx[ax] = ref + d
+    ext = idx.max(axis=1) - idx.min(axis=1)
+    ax = int(np.argmax(ext))
+    cut = np.median(idx[ax])
+    side = (idx[ax] > cut).astype(np.int64) + 1
+    if side.min() == side.max():
+        side = (idx[ax] >= cut).astype(np.int64) + 1
+    pieces = np.zeros(arr.size, np.int64)
+    nxt = 1
+    for sd in (1, 2):
+        sel = np.zeros(arr.size, bool)
+        sel[cells[side == sd]] = True
+        comp, nc = ndimage.label(sel.reshape(shape), structure=_face_structure(len(shape)))
+        comp = comp.ravel()
+        for c in range(1, nc + 1):
+            pieces[comp == c] = nxt
+            nxt += 1
+    return pieces
+
+
+def _split_large(lab, arr, amap, periodic, dist, flat_d, w0, max_cells):
+    """Split every region larger than `max_cells` by a watershed of the distance restricted to it, with
+    marker windows w0 - 1, w0 - 2, ... 1 (the first that gives at least two markers), recursively.
+    A piece that touches no solid joins the neighbouring piece it shares most faces with."""
+    lab = lab.copy()
+    nxt = int(lab.max()) + 1
+    todo = [int(l) for l in np.unique(lab[lab > 0])]
+    while todo:
+        l = todo.pop()
+        cells = np.flatnonzero(lab == l)
+        if cells.size <= max_cells:
+            continue
+        inside = np.zeros(arr.size, bool)
+        inside[cells] = True
+        inside = inside.reshape(arr.shape)
+        d_in = np.where(inside, dist, 0.0)
+        pieces = None
+        for w in range(max(w0 - 1, 1), 0, -1):
+            peak = _markers(d_in, inside, amap, periodic, w)
+            plab, npk = ndimage.label(peak, structure=np.ones((3,) * arr.ndim, bool))
+            if npk >= 2:
+                seeds = plab.ravel().astype(np.int64)
+                pieces = _flood(inside, amap, periodic, flat_d, seeds)
+                break
+        if pieces is None:
+            pieces = _bisect(cells, arr, amap, periodic)
+        ids = [int(q) for q in np.unique(pieces[cells]) if q > 0]
+        # pieces that touch no solid join their best-connected neighbouring piece
+        good = {q for q in ids if _touches_solid(np.flatnonzero(pieces == q), arr, amap, periodic)}
+        if not good:
+            continue
+        for q in ids:
+            if q in good:
+                continue
+            sub = pieces.copy()
+            sub[(sub > 0) & ~np.isin(sub, [q] + sorted(good))] = 0
+            contacts = _region_contacts(sub.reshape(arr.shape), arr, amap, periodic)
+            best, cnt = None, -1
+            for (a, b), c in sorted(contacts.items()):
+                other = b if a == q else (a if b == q else None)
+                if other is not None and other in good and c > cnt:
+                    best, cnt = other, c
+            if best is not None:
+                pieces[pieces == q] = best
+        kept = sorted({int(q) for q in np.unique(pieces[cells]) if q > 0})
+        if len(kept) < 2:
+            continue
+        for k, q in enumerate(kept):
+            sel = cells[pieces[cells] == q]
+            if k == 0:
+                new = l
+            else:
+                new = nxt
+                nxt += 1
+            lab[sel] = new
+            todo.append(new)
+    return lab
+
+
 def _region_contacts(lab, arr, amap, periodic):
     """Face contacts between distinct regions: dict (a, b) -> count with a < b."""
     L3 = lab.reshape(arr.shape)
@@ -409,7 +519,7 @@ def _merge_regions(lab, arr, amap, periodic, min_cells, max_cells, target):
 
 
 def label_pores(mask: np.ndarray, target: int, periodic=X_PERIODIC, windows=range(1, 25), method="window",
-                min_cells: int = 0, max_cells: int = 0, oversegment: float = 4.0) -> Labelling:
+                min_cells: int = 0, max_cells: int = 0, oversegment: float = 4.0, split_cells: int = 0) -> Labelling:
     """Watershed decomposition of the void into about `target` pores (heights: the distance to the
     solid; priority flood, highest distance first, ties by insertion order, over the face-connected
     void wrapping along periodic axes).
@@ -424,7 +534,12 @@ def label_pores(mask: np.ndarray, target: int, periodic=X_PERIODIC, windows=rang
     `target` remain and none is below min_cells (0 disables a bound).  Merged regions can carry
     appendages that touch no solid; under the closure of Eqs. 6/9 a constant velocity there is a null
     vector of the closure block (seen on a 96^3 sphere pack), so the workloads use "window".
-    Void components without a marker get one at their deepest cell (lowest linear index among ties)."""
+    Void components without a marker get one at their deepest cell (lowest linear index among ties).
+
+    split_cells > 0 (window method only): every region larger than split_cells is re-segmented, by a
+    watershed of the distance restricted to it with smaller marker windows, or, when it has a single
+    distance maximum, by a median bisection along its longest extent; a piece that touches no solid
+    joins the neighbouring piece it shares most faces with."""
     m = np.asarray(mask).astype(bool)
     arr, amap = _squeeze2d(m)
     dist2 = _squeeze2d(distance_to_solid(m, periodic))[0]
@@ -478,6 +593,8 @@ def label_pores(mask: np.ndarray, target: int, periodic=X_PERIODIC, windows=rang
             nl += 1
             lab[c] = nl
     lab = _flood(arr, amap, periodic, flat_d, lab)
+    if method == "window" and split_cells > 0:
+        lab = _split_large(lab, arr, amap, periodic, dist2, flat_d, int(chosen), split_cells)
     if method == "nms":
         lab = _merge_regions(lab, arr, amap, periodic, min_cells, max_cells or arr.size,
                              target if (min_cells or max_cells) else arr.size)
@@ -555,6 +672,7 @@ def make_workload(kind: str, seed: int = 0, **kw) -> Workload:
           'tiny2d' / 'tiny3d'  small disk/sphere packs for brute-force checks (n given by kw)"""
     per = X_PERIODIC
     min_cells = max_cells = 0
+    split = 0
     if kind == "disks64":
         n = kw.get("n", 64)
         mask = disk_pack_2d(n, kw.get("n_disks", 12), 4.0, 8.0, seed)
@@ -569,6 +687,10 @@ def make_workload(kind: str, seed: int = 0, **kw) -> Workload:
         mask = gaussian_field_3d(n, kw.get("corr_len", 8.0), kw.get("porosity", 0.20), seed)
         target = kw.get("target", 3000)
         min_cells, max_cells = 135, 5400
+        # split_cells > 0 re-segments regions above that many cells (watershed inside the region, else a
+        # median bisection) so that dense local inverses of the largest pores (up to ~27,000 cells at
+        # 256^3) fit the device; off by default (see the labeller's split_cells)
+        split = kw.get("split_cells", 0)
     elif kind == "tiny2d":
         n = kw.get("n", 16)
         mask = disk_pack_2d(n, kw.get("n_disks", 2), kw.get("rmin", 1.5), kw.get("rmax", 3.0), seed)
@@ -581,5 +703,5 @@ def make_workload(kind: str, seed: int = 0, **kw) -> Workload:
         raise ValueError(kind)
     mask, dropped = percolating_void(mask, per)
     lab = label_pores(mask, target, per, method=kw.get("method", "window"), min_cells=kw.get("min_cells", min_cells),
-                      max_cells=kw.get("max_cells", max_cells))
+                      max_cells=kw.get("max_cells", max_cells), split_cells=split)
     return Workload(kind, mask, lab.labels, per, dropped, lab.n_labels)
