@@ -219,3 +219,36 @@ def proposal(out, x_stokes, shape, U, P):
     o = out[0]
     corr = np.concatenate([(o[0] * U).ravel(), (o[1] * U).ravel(), (o[2] * U).ravel(), (o[3] * P).ravel()])
     return np.asarray(x_stokes, np.float64) + corr
+
+
+# ----------------------------------------------------------------------------------------------
+# training
+# ----------------------------------------------------------------------------------------------
+def masked_mse(out, target, weight):
+    """L = sum(weight * (out - target)^2) / sum(weight) over every channel; returns (L, dL/dout).
+    `weight` (N, 1, D, H, W) restricts the loss to the cells that carry unknowns (1 on void, 0 solid)."""
+    w = np.broadcast_to(weight, out.shape)
+    den = float(w.sum())
+    d = out - target
+    return float((w * d * d).sum() / den), 2.0 * w * d / den
+
+
+class Adam:
+    """Adam (Kingma & Ba, 2015) with the bias-corrected moments:
+    m <- b1 m + (1 - b1) g,  v <- b2 v + (1 - b2) g^2,  theta <- theta - lr m_hat / (sqrt(v_hat) + eps)."""
+
+    def __init__(self, params, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
+        self.lr, self.b1, self.b2, self.eps = lr, b1, b2, eps
+        self.m = {k: np.zeros_like(v) for k, v in params.items()}
+        self.v = {k: np.zeros_like(v) for k, v in params.items()}
+        self.t = 0
+
+    def step(self, params, grads):
+        self.t += 1
+        c1 = 1.0 - self.b1 ** self.t
+        c2 = 1.0 - self.b2 ** self.t
+        for k in params:
+            g = grads[k]
+            self.m[k] = self.b1 * self.m[k] + (1.0 - self.b1) * g
+            self.v[k] = self.b2 * self.v[k] + (1.0 - self.b2) * g * g
+            params[k] -= self.lr * (self.m[k] / c1) / (np.sqrt(self.v[k] / c2) + self.eps)
