@@ -135,10 +135,6 @@ __global__ void k_f2bf(const float* __restrict__ in, __nv_bfloat16* __restrict__
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     out[i] = __float2bfloat16_rn(in[i]);
 }
-__global__ void k_d2f_any(const double* __restrict__ in, float* __restrict__ out, long long n) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-    out[i] = (float)in[i];
-}
 template <typename VT>
 __global__ void k_sum3(const VT* __restrict__ a, const VT* __restrict__ b, const VT* __restrict__ c,
                        double* __restrict__ z, long long n) {
