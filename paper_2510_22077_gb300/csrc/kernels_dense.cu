@@ -21,9 +21,7 @@ namespace {
 
 constexpr int TB = 64;   // Gauss-Jordan panel width == tile edge
 
-template <typename T> __device__ __forceinline__ T to_acc(T v) { return v; }
 __device__ __forceinline__ float to_f(float v) { return v; }
-__device__ __forceinline__ float to_f(__nv_bfloat16 v) { return __bfloat162float(v); }
 __device__ __forceinline__ double to_f(double v) { return v; }
 
 __device__ __forceinline__ int find_block(const long long* __restrict__ off, int nb, long long t) {
