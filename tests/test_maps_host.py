@@ -91,3 +91,21 @@ def test_maps_host_hand_fixtures(name, n_dilate, n_tag):
     assert np.array_equal(got["dual_count"], cnt)
     assert got["n_prim"] == m.n_prim and got["n_iface"] == m.n_iface
     assert got["n_dropped_labels"] == len(m.dropped_labels)
+
+
+@pytest.mark.parametrize("kind,kw,seed", [("tiny3d", dict(n=8), 1), ("tiny3d", dict(n=10, porosity=0.55), 2),
+                                          ("tiny2d", dict(n=20, n_disks=3), 5), ("spheres", dict(n=32), 0)])
+@pytest.mark.parametrize("n_dilate,n_tag", [(1, 1), (2, 2), (0, 1)])
+def test_maps_host_seeded_images_all_depths(kind, kw, seed, n_dilate, n_tag):
+    w = inputs.make_workload(kind, seed=seed, **kw)
+    pb = krylov.Problem(w.mask, w.labels, mac.Params(1.0, 1.0, (1.0, 0.0, 0.0)), w.periodic, n_dilate, n_tag)
+    m, g = pb.maps, pb.g
+    got = pns.pns_maps_host(w.mask, w.labels, w.periodic, n_dilate, n_tag)
+    assert np.array_equal(got["cell_prim"], m.cell_prim) and np.array_equal(got["cell_iface"], m.cell_iface)
+    for d in range(g.dim):
+        assert np.array_equal(got["face_class"][d], m.face_class[d])
+        assert np.array_equal(got["tags"][d], m.tags[d])
+    cnt = np.zeros(g.nfull, np.int32)
+    for u in m.dual_unknowns:
+        cnt[u] += 1
+    assert np.array_equal(got["dual_count"], cnt)
