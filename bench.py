@@ -55,6 +55,10 @@ def parse(argv=None):
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--precisions", default="fp64,fp32,bf16",
+                    help="local-inverse precisions to time once each on the --precision-n pack at N=1 "
+                         "(results under 'precisions'; 'none' to skip)")
+    ap.add_argument("--precision-n", type=int, default=48)
     ap.add_argument("--compare", default="aplmm_s,block_schur",
                     help="comma-separated preconditioner variants to time once each after the main run at N=1 "
                          "(results under 'variants'; 'none' to skip)")
@@ -209,25 +213,50 @@ print(json.dumps({"total_s": total, "maps_s": t_maps, "asm_s": t_asm, "build_s":
 def compare_variants(args, w, mu):
     """One solve per named variant on the same workload (fresh context each): wall time on the
     library's stream, iteration counts, build time."""
-    import torch
-    from paper_2510_22077_gb300 import pns
     out = {}
     for var in [v.strip() for v in args.compare.split(",") if v.strip()]:
-        S = pns.Solver(w.mask, w.labels, 1.0, mu, (1.0, 0.0, 0.0), variant=var, precision=args.precision,
+        out[var] = one_solve(w, mu, var, args.precision)
+    return out
+
+
+def one_solve(w, mu, variant, precision):
+    """One timed solve (Stokes guess, build, Newton) in a fresh context; errors are recorded, not raised,
+    so that a failing comparison never costs the main line."""
+    import torch
+    from paper_2510_22077_gb300 import pns
+    S = None
+    try:
+        S = pns.Solver(w.mask, w.labels, 1.0, mu, (1.0, 0.0, 0.0), variant=variant, precision=precision,
                        timing=True)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
         e0.record(S.stream)
         x = S.zeros()
-        _, sst = S.pns_stokes_solve(x)
+        _, sst = S.pns_stokes_solve(x, check=False)
         S.pns_build_precond(x)
         st = S.pns_newton_solve(x, check=False)
         e1.record(S.stream)
         torch.cuda.synchronize()
-        out[var] = {"ms": e0.elapsed_time(e1), "status": st["status"], "newton_its": st["newton_its"],
-                    "fgmres_its_stokes": sst["fgmres_its_total"], "fgmres_its_newton": st["fgmres_its"],
-                    "t_build_ms": st["t_ml_ms"] + st["t_mg_ms"], "final_res": st["res_hist"][-1] if st["res_hist"] else None}
-        S.close()
+        return {"ms": e0.elapsed_time(e1), "status": st["status"], "stokes_status": sst["status"],
+                "newton_its": st["newton_its"], "fgmres_its_stokes": sst["fgmres_its_total"],
+                "fgmres_its_newton": st["fgmres_its"], "t_build_ms": st["t_ml_ms"] + st["t_mg_ms"],
+                "final_res": st["res_hist"][-1] if st["res_hist"] else None}
+    except Exception as e:   # recorded in the JSON line
+        return {"error": f"{type(e).__name__}: {e}"[:300]}
+    finally:
+        if S is not None:
+            S.close()
+
+
+def compare_precisions(args):
+    """gPLMM with FP64, FP32 and BF16 local inverses on the smaller sphere pack (an FP64 Gauss-Jordan
+    build of the 96^3 pack takes minutes on the FP64 units): time to 1e-8 and iterations of each."""
+    from paper_2510_22077_gb300 import inputs
+    w = inputs.make_workload("spheres", seed=args.seed, n=args.precision_n)
+    mu = inputs.mu_kozeny_carman(w.mask, args.re)
+    out = {"workload": f"spheres{args.precision_n}^3 phi=0.35 seed={args.seed}, gPLMM, Re~{args.re:g}"}
+    for prec in [p.strip() for p in args.precisions.split(",") if p.strip()]:
+        out[prec] = one_solve(w, mu, "gplmm", prec)
     return out
 
 
@@ -350,6 +379,8 @@ def main():
                        "d2h_bytes_per_step": int(host.nbytes)}
     if rank == 0 and world == 1 and args.compare and args.compare != "none":
         line["variants"] = compare_variants(args, w, mu)
+    if rank == 0 and world == 1 and args.precisions and args.precisions != "none":
+        line["precisions"] = compare_precisions(args)
     if rank == 0 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(w, mu, its_stokes + its_newton)
     if rank == 0:
