@@ -13,6 +13,7 @@ Modules
     krylov  -- right-preconditioned flexible GMRES, Newton, backward-Euler stepping  (Sec. 8, Eq. 3)
     block   -- block-triangular Schur comparator with the scaled BFBt approximation  (Sec. 1, Eq. 4)
     unet    -- 3D U-Net of the learned initial guess: NumPy forward and explicit backward, sample encoding
+    coarse_solver -- coarse-scale Navier-Stokes solver: Newton on the coarse unknowns  (Sec. 5, Alg. 1)
 
 Parity status: every function is pinned by a test in tests/test_oracle_*.py against something
 other than itself (closed forms, finite differences, brute-force dense solves, the projection
