@@ -158,6 +158,8 @@ void pns_destroy(pns_ctx* ctx);
 /* Message of the last error on this context ("" if none).  Valid until the next call. */
 const char* pns_last_error(const pns_ctx* ctx);
 
+/* Fill the HOST struct `info` with the sizes of the context's problem: grid, unknown counts,
+ * primary/dual block statistics, device bytes held.  PNS_ERR_ARG if ctx or info is NULL. */
 int pns_get_info(const pns_ctx* ctx, pns_info* info);
 
 /* r = r(x) (Eq. 3): the Newton residual in FP64.  x_prev: previous time level (device, full
