@@ -223,25 +223,32 @@ class Solver:
         return inf.as_dict()
 
     def pns_residual(self, x, x_prev=None, r=None):
+        """r(x), the FP64 Newton residual (steady, or backward Euler from x_prev); CUDA tensors of the full
+        layout [u_x | u_y | (u_z) | p], entries that are not unknowns ignored on input, 0 on output."""
         r = self.zeros() if r is None else r
         self._check(self.lib.pns_residual(self.ctx, _ptr(x), _ptr(x_prev), _ptr(r)), "pns_residual")
         return r
 
     def pns_jacobian_apply(self, x_lin, v, y=None):
+        """y = J(x_lin) v, the Newton Jacobian at x_lin (upwind branches frozen there)."""
         y = self.zeros() if y is None else y
         self._check(self.lib.pns_jacobian_apply(self.ctx, _ptr(x_lin), _ptr(v), _ptr(y)), "pns_jacobian_apply")
         return y
 
     def pns_operator_apply(self, variant, x_lin, v, y=None):
+        """y = A_b v for the build matrix of `variant` at x_lin (gplmm: the modified Jacobian of the
+        inertia-free tagged faces; aplmm_ns: the Newton Jacobian; aplmm_s: the Stokes operator)."""
         y = self.zeros() if y is None else y
         var = VARIANTS[variant] if isinstance(variant, str) else int(variant)
         self._check(self.lib.pns_operator_apply(self.ctx, var, _ptr(x_lin), _ptr(v), _ptr(y)), "pns_operator_apply")
         return y
 
     def pns_build_precond(self, x_lin):
+        """Build the context's preconditioner at the linearisation state x_lin (synchronises)."""
         self._check(self.lib.pns_build_precond(self.ctx, _ptr(x_lin)), "pns_build_precond")
 
     def pns_precond_apply(self, v, z=None):
+        """z = M^{-1} v with the built preconditioner (FP64 in and out)."""
         z = self.zeros() if z is None else z
         self._check(self.lib.pns_precond_apply(self.ctx, _ptr(v), _ptr(z)), "pns_precond_apply")
         return z
@@ -253,6 +260,9 @@ class Solver:
         return z
 
     def pns_newton_solve(self, x, x_prev=None, check=True):
+        """Newton-FGMRES from the initial guess x, updated in place; returns the statistics as a dict
+        (status, iterations per Newton step, residual history, build and solve times).  With
+        check=False a non-converged solve returns its status instead of raising."""
         st = Stats()
         rc = self.lib.pns_newton_solve(self.ctx, _ptr(x), _ptr(x_prev), ctypes.byref(st))
         if check:
@@ -262,6 +272,7 @@ class Solver:
         return d
 
     def pns_stokes_solve(self, x=None, check=True):
+        """The Stokes solution (the usual Newton initial guess); returns (x, statistics)."""
         x = self.zeros() if x is None else x
         st = Stats()
         rc = self.lib.pns_stokes_solve(self.ctx, _ptr(x), ctypes.byref(st))
@@ -281,6 +292,8 @@ class Solver:
         return a
 
     def pns_export_maps(self):
+        """The integer maps of the context (primary grid and interface of each cell, face classes, gPLMM
+        tags, dual-grid multiplicity of each unknown, pinned cells) as NumPy arrays."""
         nc, dim = self.ncell, self.dim
         cell_prim = np.zeros(nc, np.int32)
         cell_iface = np.zeros(nc, np.int32)
