@@ -102,10 +102,12 @@ typedef struct pns_options {
   void* stream;          /* cudaStream_t to enqueue on (NULL = legacy default stream) */
   int block_inner_its;   /* PNS_BLOCK_SCHUR: inner GMRES iterations per solve with F or L (default 20) */
   double block_inner_tol;/* PNS_BLOCK_SCHUR: inner GMRES relative tolerance (default 1e-2) */
-  int gj_tensor_cores;   /* FP32 Gauss-Jordan update: 0 (default) FP32 FMA units; 1 tensor cores
-                            through warp-level mma.sync, TF32 with a 3-term split (hi*hi + hi*lo +
-                            lo*hi, close to FP32 accuracy).  Measured on a GB300 on the 96^3 sphere pack:
-                            34.6 TFLOP/s against 39.8 for the FMA kernel, hence the default */
+  int gj_tensor_cores;   /* FP32 Gauss-Jordan trailing update of the local inverses:
+                            0 FP32 FMA units;
+                            1 tensor cores through warp-level mma.sync, TF32 with a 3-term split (hi*hi +
+                              hi*lo + lo*hi, close to FP32 accuracy);
+                            2 5th-generation tensor cores (tcgen05.mma kind::tf32, accumulator in TMEM,
+                              operands staged by TMA), with the same 3-term split */
 } pns_options;
 
 typedef struct pns_stats {
@@ -137,6 +139,10 @@ typedef struct pns_info {
   double prim_sum_n2, dual_sum_n2;  /* sum of squared block sizes (dense inverse entries) */
   int max_block;
   size_t device_bytes;              /* bytes the context holds on the device */
+  size_t static_scratch_capacity;   /* size of the fixed array of pns_precond_apply_static (bytes) */
+  size_t static_apply_bytes;        /* bytes one pns_precond_apply_static of the built preconditioner takes
+                                       from that array (0 before a build or for BLOCK_SCHUR); the call is
+                                       refused when this exceeds static_scratch_capacity */
 } pns_info;
 
 /* Fill `opt` with the defaults listed above. */
@@ -184,15 +190,25 @@ int pns_build_precond(pns_ctx* ctx, const double* x_lin);
  * PNS_ERR_STATE before pns_build_precond. */
 int pns_precond_apply(pns_ctx* ctx, const double* v, double* z);
 
-/* z = M^{-1} v exactly as pns_precond_apply, but without allocating device memory during the call:
- * for callers that cannot call cudaMalloc when they apply the preconditioner (a device allocator
- * owned by someone else, or a footprint that must stay fixed after start-up).  The scratch vectors
- * live in one file-scope device array of 24 MiB, enough for a full layout of about 500,000 entries;
- * larger problems return PNS_ERR_ARG with a message.  The array is shared by every call in the
- * process, so calls that overlap on the GPU race on it.  Its device address is looked up once per
- * device on the first call with that device current: make that first call before any stream capture.
+/* z = M^{-1} v exactly as pns_precond_apply (the same apply body), but without allocating device
+ * memory during the call: for callers that cannot call cudaMalloc when they apply the preconditioner
+ * (a device allocator owned by someone else, or a footprint that must stay fixed after start-up).
+ * The scratch vectors live in one file-scope device array of 24 MiB.  One apply takes
+ *     5 * A(8 * nfull) + A(w * P) + R + 2 * A(8 * n_o)  bytes of it,
+ * with nfull = (dim + 1) * ncell, P = the larger of the primary and dual packed sizes (block sizes
+ * rounded up to 8, summed), A(x) = x rounded up to a multiple of 256, w = 8 for FP64 and 4 for FP32 /
+ * BF16 preconditioners, R = A(8 * P) when the local solves are refined (refine_steps == -1, FP32 /
+ * BF16) and 0 otherwise; pns_get_info reports the figure (static_apply_bytes).  Larger problems
+ * return PNS_ERR_ARG with a message; a full layout of up to about 500,000 entries fits.
+ * The array is shared by every call in the process and keeps the last call's contents (each call
+ * writes every entry it reads first), so calls that overlap on the GPU race on it: serialise them.
+ * Its device address is taken once per device inside pns_setup, with the context's device current;
+ * the call itself only reads that address.  Under lazy module loading (the CUDA default) the code of
+ * a kernel is loaded on its first launch in the process: a caller for whom even that must not happen
+ * inside this call runs one pns_precond_apply first, or loads modules eagerly.
  * Every GPU that loads the library holds the array until exit.  The paper has no counterpart: this is
- * an interface of this library.  PNS_ERR_STATE before pns_build_precond. */
+ * an interface of this library.  PNS_ERR_STATE before pns_build_precond, PNS_ERR_ARG for the
+ * BLOCK_SCHUR variant. */
 int pns_precond_apply_static(pns_ctx* ctx, const double* v, double* z);
 
 /* Newton-FGMRES (Sec. 8).  x: device, full layout; initial guess on input, solution on output.

@@ -130,7 +130,31 @@ struct Ctx {
   double t_setup_ms = 0;
   double t_mg_ms = 0, t_ml_ms = 0;
   GjTimer gj;                    // update-kernel timing of the local-inverse builds (timing == 1)
+  void* static_scratch = nullptr;  // device address of the fixed scratch array of pns_precond_apply_static
+  std::string static_err;        // why that address could not be taken at set-up ("" if it was)
 };
+
+// Scratch of one preconditioner apply: FP64 vectors of the full layout (zG, t1, zd, t2, zp), the packed
+// local vectors in the working type (pk; max(prim, dual) n_total entries), the packed FP64 refined local
+// solutions (zpk; only with apply_refine) and the two coarse vectors (n_o entries each).
+struct ApplyScratch {
+  double *zG = nullptr, *t1 = nullptr, *zd = nullptr, *t2 = nullptr, *zp = nullptr;
+  void* pk = nullptr;
+  double* zpk = nullptr;
+  double *crhs = nullptr, *cx = nullptr;
+  bool timed = false;            // record CUDA events around the batched local solves
+};
+
+// z = M^{-1} v (Eqs. 4a, 24, 25, 20) with the given scratch; the context's own apply and the
+// allocation-free apply of pns_static.cu both run this body.
+int precond_apply_with(Ctx& C, Precond& pc, const double* v, double* z, const ApplyScratch& W);
+
+// The allocation-free apply (pns_static.cu): device address of its fixed array on the current device,
+// taken once per device at context set-up; the array's size; the bytes one apply of a built
+// preconditioner takes from it.
+cudaError_t static_scratch_init(void** addr);
+size_t static_scratch_capacity();
+size_t static_apply_bytes(const Ctx& C);
 
 // Counts every kernel launch of the library (all contexts); read through pns_stats.
 void count_launch();
@@ -147,6 +171,21 @@ cudaError_t launch_cast_f2d(const float* in, double* out, long long n, cudaStrea
 // dense local blocks
 template <typename ST>
 cudaError_t launch_assemble(const Ctx& C, const BlockSet& B, int op, const double* state, ST* mat, int closure);
+// Gauss-Jordan trailing update on the 5th-generation tensor cores (kernels_gj_tc.cu): per build of one
+// block set, setup() makes the split-panel buffers and the tensor maps of the blocks; step() runs the
+// panel split and the update of panel step k for the first cnt blocks of `order`.
+struct GjTcImpl;
+struct GjTc {
+  GjTcImpl* impl;
+  GjTc();
+  ~GjTc();
+  GjTc(const GjTc&) = delete;
+  GjTc& operator=(const GjTc&) = delete;
+  cudaError_t setup(const BlockSet& B, float* mat, cudaStream_t s);
+  cudaError_t step(const BlockSet& B, float* mat, int k, int cnt, const int* d_order, const long long* d_pre2,
+                   long long ntiles, const std::vector<int>& order, int* d_bad, cudaStream_t s);
+};
+
 template <typename ST>
 cudaError_t launch_gj_invert(const BlockSet& B, ST* mat, int* d_bad, cudaStream_t s, GjTimer* timer = nullptr,
                              int tensor_cores = 0);

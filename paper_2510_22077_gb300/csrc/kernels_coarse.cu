@@ -113,7 +113,7 @@ __global__ void k_cpiv(double* __restrict__ A, int n, int t, double* __restrict_
   int p = bi[0];
   double pv = A[(long long)p * n + t];
   if (!(bv[0] > 0.0) || !(bv[0] < 1e300)) {
-    if (threadIdx.x == 0) atomicExch(bad, 1);
+    if (threadIdx.x == 0) atomicOr(bad, 1);
     pv = 1.0;
   }
   if (threadIdx.x == 0) perm[t] = p;

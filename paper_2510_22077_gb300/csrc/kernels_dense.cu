@@ -134,7 +134,7 @@ __global__ void __launch_bounds__(256) k_gj_diag(int k, const int* __restrict__ 
     ST piv = s_piv;
     const bool okp = (piv == piv) && piv != (ST)0 && (double)fabs((double)piv) < 1e300;
     if (!okp) {
-      if (threadIdx.x == 0) atomicExch(bad, 1);
+      if (threadIdx.x == 0) atomicOr(bad, 1);
       piv = (ST)1;
     }
     const ST inv = (ST)1 / piv;
@@ -1102,7 +1102,7 @@ __global__ void k_bpiv(int t, const int* __restrict__ order, const int* __restri
   int p = bi[0];
   double pv = A[(long long)p * k + t];
   if (!(bv[0] > 0.0) || !(bv[0] < 1e300)) {
-    if (threadIdx.x == 0) atomicExch(bad, 1);
+    if (threadIdx.x == 0) atomicOr(bad, 1);
     pv = 1.0;
   }
   if (threadIdx.x == 0) perm[koff[b] + t] = p;
@@ -1300,6 +1300,15 @@ cudaError_t launch_gj_invert(const BlockSet& B, ST* mat, int* d_bad, cudaStream_
   }
   else
     cudaFuncSetAttribute(k_gj_update<ST, TBK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  // tensor_cores == 2: the update on the 5th-generation tensor cores (FP32 inverses only)
+  GjTc tc5;
+  const bool use_tc5 = std::is_same<ST, float>::value && tensor_cores == 2;
+  if (use_tc5) {
+    if ((e = tc5.setup(B, (float*)mat, s)) != cudaSuccess) {
+      cudaFree(d_order); cudaFree(d_pre1); cudaFree(d_pre2);
+      return e;
+    }
+  }
   int Tmax = T[order[0]];
   int cnt = B.nblk;
   for (int k = 0; k < Tmax; ++k) {
@@ -1325,14 +1334,19 @@ cudaError_t launch_gj_invert(const BlockSet& B, ST* mat, int* d_bad, cudaStream_
             }
             tiles += pre2[cnt];
           }
-          pns::count_launch();
-          if (tensor_cores)
+          if (use_tc5) {
+            if ((e = tc5.step(B, (float*)mat, k, cnt, d_order, d_pre2, pre2[cnt], order, d_bad, s)) != cudaSuccess)
+              break;
+          } else if (tensor_cores) {
+            pns::count_launch();
             k_mm128_gj_update_tc<<<(unsigned)pre2[cnt], 256, smem_mm, s>>>(k, cnt, d_order, d_pre2, B.d_n.as<int>(),
                                                                            B.d_ld.as<int>(), B.d_moff.as<long long>(),
                                                                            mat);
-          else
+          } else {
+            pns::count_launch();
             k_mm128_gj_update<<<(unsigned)pre2[cnt], 256, smem_mm, s>>>(k, cnt, d_order, d_pre2, B.d_n.as<int>(),
                                                                         B.d_ld.as<int>(), B.d_moff.as<long long>(), mat);
+          }
           if (timer) cudaEventRecord(evs.back(), s);
         } else {
           pns::count_launch();
@@ -1439,6 +1453,28 @@ template cudaError_t launch_local_solve<float, float>(const BlockSet&, const flo
 template cudaError_t launch_local_solve<__nv_bfloat16, float>(const BlockSet&, const __nv_bfloat16*, const double*,
                                                               double*, float*, int, cudaStream_t);
 
+// Temporary device buffers of one host-side step; every allocation is checked, and everything is freed
+// when the object goes out of scope.
+struct TmpDev {
+  std::vector<void*> ptrs;
+  TmpDev() = default;
+  TmpDev(const TmpDev&) = delete;
+  TmpDev& operator=(const TmpDev&) = delete;
+  ~TmpDev() {
+    for (void* p : ptrs) cudaFree(p);
+  }
+  template <typename T>
+  cudaError_t get(T** out, size_t bytes) {
+    *out = nullptr;
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, std::max<size_t>(bytes, 1));
+    if (e != cudaSuccess) return e;
+    ptrs.push_back(p);
+    *out = (T*)p;
+    return cudaSuccess;
+  }
+};
+
 // Refine the inverses of a block set: blocks whose max |I - A X| exceeds `thresh` get `steps`
 // Newton-Schulz steps.  Scratch is bounded by `budget_bytes` (blocks processed in chunks).
 template <typename ST, typename AT>
@@ -1479,12 +1515,13 @@ cudaError_t launch_ns_refine(const Ctx& C, const BlockSet& B, int op, const doub
       long long *d_pre = nullptr, *d_soff = nullptr;
       unsigned int* d_rmax = nullptr;
       AT *R = nullptr, *T = nullptr;
-      if ((e = cudaMalloc(&d_lst, sizeof(int) * nent)) != cudaSuccess) break;
-      cudaMalloc(&d_pre, sizeof(long long) * (nent + 1));
-      cudaMalloc(&d_soff, sizeof(long long) * (nent + 1));
-      cudaMalloc(&d_rmax, sizeof(unsigned int) * nent);
-      if ((e = cudaMalloc(&R, sizeof(AT) * soff[nent])) != cudaSuccess) { cudaFree(d_lst); break; }
-      if ((e = cudaMalloc(&T, sizeof(AT) * soff[nent])) != cudaSuccess) { cudaFree(d_lst); cudaFree(R); break; }
+      TmpDev tmp;
+      if ((e = tmp.get(&d_lst, sizeof(int) * nent)) != cudaSuccess) break;
+      if ((e = tmp.get(&d_pre, sizeof(long long) * (nent + 1))) != cudaSuccess) break;
+      if ((e = tmp.get(&d_soff, sizeof(long long) * (nent + 1))) != cudaSuccess) break;
+      if ((e = tmp.get(&d_rmax, sizeof(unsigned int) * nent)) != cudaSuccess) break;
+      if ((e = tmp.get(&R, sizeof(AT) * soff[nent])) != cudaSuccess) break;
+      if ((e = tmp.get(&T, sizeof(AT) * soff[nent])) != cudaSuccess) break;
       cudaMemsetAsync(T, 0, sizeof(AT) * soff[nent], s);
       cudaMemcpyAsync(d_lst, lst.data(), sizeof(int) * nent, cudaMemcpyHostToDevice, s);
       cudaMemcpyAsync(d_pre, rowpre.data(), sizeof(long long) * (nent + 1), cudaMemcpyHostToDevice, s);
@@ -1522,10 +1559,11 @@ cudaError_t launch_ns_refine(const Ctx& C, const BlockSet& B, int op, const doub
         ssoff.push_back(0);
         int* d_sel = nullptr;
         long long *d_tpre = nullptr, *d_epre = nullptr, *d_ssoff = nullptr;
-        cudaMalloc(&d_sel, sizeof(int) * ns);
-        cudaMalloc(&d_tpre, sizeof(long long) * (ns + 1));
-        cudaMalloc(&d_epre, sizeof(long long) * (ns + 1));
-        cudaMalloc(&d_ssoff, sizeof(long long) * (ns + 1));
+        TmpDev tsel;
+        if ((e = tsel.get(&d_sel, sizeof(int) * ns)) != cudaSuccess) break;
+        if ((e = tsel.get(&d_tpre, sizeof(long long) * (ns + 1))) != cudaSuccess) break;
+        if ((e = tsel.get(&d_epre, sizeof(long long) * (ns + 1))) != cudaSuccess) break;
+        if ((e = tsel.get(&d_ssoff, sizeof(long long) * (ns + 1))) != cudaSuccess) break;
         cudaMemcpyAsync(d_sel, sel.data(), sizeof(int) * ns, cudaMemcpyHostToDevice, s);
         cudaMemcpyAsync(d_tpre, tpre.data(), sizeof(long long) * (ns + 1), cudaMemcpyHostToDevice, s);
         cudaMemcpyAsync(d_epre, epre.data(), sizeof(long long) * (ns + 1), cudaMemcpyHostToDevice, s);
@@ -1544,17 +1582,7 @@ cudaError_t launch_ns_refine(const Ctx& C, const BlockSet& B, int op, const doub
             d_sel, d_epre, ns, B.d_n.as<int>(), B.d_ld.as<int>(), B.d_moff.as<long long>(), mat, d_ssoff, T); }
         e = cudaStreamSynchronize(s);
         if (e == cudaSuccess) e = cudaGetLastError();
-        cudaFree(d_sel);
-        cudaFree(d_tpre);
-        cudaFree(d_epre);
-        cudaFree(d_ssoff);
       }
-      cudaFree(d_lst);
-      cudaFree(d_pre);
-      cudaFree(d_soff);
-      cudaFree(d_rmax);
-      cudaFree(R);
-      cudaFree(T);
       if (sel.empty()) break;
     }
   }
@@ -1574,11 +1602,11 @@ cudaError_t launch_ns_refine(const Ctx& C, const BlockSet& B, int op, const doub
     int* d_lst = nullptr;
     long long *d_pre = nullptr, *d_soff = nullptr;
     unsigned int* d_rmax = nullptr;
-    if ((e = cudaMalloc(&R, sizeof(AT) * maxm)) == cudaSuccess) {
-      cudaMalloc(&d_lst, sizeof(int));
-      cudaMalloc(&d_pre, sizeof(long long) * 2);
-      cudaMalloc(&d_soff, sizeof(long long) * 2);
-      cudaMalloc(&d_rmax, sizeof(unsigned int));
+    TmpDev tmp;
+    if ((e = tmp.get(&R, sizeof(AT) * maxm)) == cudaSuccess && (e = tmp.get(&d_lst, sizeof(int))) == cudaSuccess &&
+        (e = tmp.get(&d_pre, sizeof(long long) * 2)) == cudaSuccess &&
+        (e = tmp.get(&d_soff, sizeof(long long) * 2)) == cudaSuccess &&
+        (e = tmp.get(&d_rmax, sizeof(unsigned int))) == cudaSuccess) {
       long long zero2[2] = {0, 0};
       cudaMemcpyAsync(d_soff, zero2, sizeof zero2, cudaMemcpyHostToDevice, s);
       for (int q = 0; q < nent && e == cudaSuccess; ++q) {
@@ -1597,11 +1625,6 @@ cudaError_t launch_ns_refine(const Ctx& C, const BlockSet& B, int op, const doub
         memcpy(&v, &rmv, sizeof v);
         *max_after = std::max(*max_after, (double)v);
       }
-      cudaFree(d_lst);
-      cudaFree(d_pre);
-      cudaFree(d_soff);
-      cudaFree(d_rmax);
-      cudaFree(R);
     }
   }
   if (e != cudaSuccess) return e;

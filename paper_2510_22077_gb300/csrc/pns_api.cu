@@ -432,6 +432,7 @@ int build_block(Ctx& C, Precond& pc) {
   C.t_mg_ms = 0;
   int hbad = 0;
   CK(cudaMemcpy(&hbad, bad.p, sizeof(int), cudaMemcpyDeviceToHost));
+  if (hbad & 2) return fail(C, PNS_ERR_TIMEOUT, "a device wait of the tensor-core Gauss-Jordan update hit its limit");
   if (hbad) return fail(C, PNS_ERR_SINGULAR, "zero or non-finite pivot in a block-Jacobi factor");
   pc.local_bytes = 0;
   for (BlockSet* B : {&pc.bs.bf, &pc.bs.bl})
@@ -591,6 +592,7 @@ int build_precond(Ctx& C, Precond& pc, int variant, const double* x_lin) {
   C.t_mg_ms = now_ms() - t1;
   int hbad = 0;
   CK(cudaMemcpy(&hbad, bad.p, sizeof(int), cudaMemcpyDeviceToHost));
+  if (hbad & 2) return fail(C, PNS_ERR_TIMEOUT, "a device wait of the tensor-core Gauss-Jordan update hit its limit");
   if (hbad) return fail(C, PNS_ERR_SINGULAR, "zero or non-finite pivot in a local or coarse factor");
   pc.ns_residual_before = pc.ns_residual_before;
   pc.local_bytes = 0;
@@ -604,9 +606,9 @@ int build_precond(Ctx& C, Precond& pc, int variant, const double* x_lin) {
 }
 
 template <typename ST, typename PT>
-int local_solve(Ctx& C, Precond& pc, BlockSet& B, const double* t, double* z, int add) {
+int local_solve(Ctx& C, Precond& pc, BlockSet& B, const double* t, double* z, int add, const ApplyScratch& W) {
   cudaEvent_t e0 = nullptr, e1 = nullptr;
-  if (C.opt.timing) {
+  if (W.timed) {
     if (C.ev_used + 2 > C.ev_pool.size()) {
       cudaEvent_t a, b;
       CK(cudaEventCreate(&a));
@@ -619,32 +621,34 @@ int local_solve(Ctx& C, Precond& pc, BlockSet& B, const double* t, double* z, in
     C.ev_used += 2;
     CK(cudaEventRecord(e0, C.stream));
   }
+  PT* pk = (PT*)W.pk;
   if constexpr (!std::is_same<ST, double>::value) {
     if (pc.apply_refine) {
-      CK((launch_local_solve_refined<ST, PT>(C, B, pc.op, pc.state.as<double>(), B.mat.as<ST>(), t, z,
-                                             C.pk_x.as<PT>(), C.zpk.as<double>(), add, C.stream)));
+      CK((launch_local_solve_refined<ST, PT>(C, B, pc.op, pc.state.as<double>(), B.mat.as<ST>(), t, z, pk, W.zpk,
+                                             add, C.stream)));
     } else {
-      CK((launch_local_solve<ST, PT>(B, B.mat.as<ST>(), t, z, C.pk_x.as<PT>(), add, C.stream)));
+      CK((launch_local_solve<ST, PT>(B, B.mat.as<ST>(), t, z, pk, add, C.stream)));
     }
   } else {
-    CK((launch_local_solve<ST, PT>(B, B.mat.as<ST>(), t, z, C.pk_x.as<PT>(), add, C.stream)));
+    CK((launch_local_solve<ST, PT>(B, B.mat.as<ST>(), t, z, pk, add, C.stream)));
   }
-  if (C.opt.timing) {
+  if (W.timed) {
     CK(cudaEventRecord(e1, C.stream));
     C.local_launches += 1;
   }
   return PNS_OK;
 }
 
+}  // namespace
+
 // z = M^{-1} v.  The local inverses, basis and coarse inverse are stored in the preconditioner's
 // precision and the batched local solves compute in it; the vectors between the stages and the two
 // stencil residual updates (v - A z_G, t - A z_d) are FP64: those differences cancel strongly when
 // z_G is large (ill-conditioned coarse systems), and in FP32 their error would scale with |A z_G|.
-int precond_apply_impl(Ctx& C, Precond& pc, const double* v, double* z) {
+int pns::precond_apply_with(Ctx& C, Precond& pc, const double* v, double* z, const ApplyScratch& W) {
   const cudaStream_t s = C.stream;
   const long long n = C.nfull;
-  double *zG = C.w1.as<double>(), *t1 = C.w2.as<double>(), *zd = C.w3.as<double>(), *t2 = C.w4.as<double>();
-  double* zp = C.w0.as<double>();
+  double *zG = W.zG, *t1 = W.t1, *zd = W.zd, *t2 = W.t2, *zp = W.zp;
   int op = pc.op;
   const double* st = pc.state.as<double>();
   if (C.opt.combine == PNS_COMBINE_CURRENT && C.cur_state) {
@@ -652,32 +656,45 @@ int precond_apply_impl(Ctx& C, Precond& pc, const double* v, double* z) {
     st = C.cur_state;
   }
   if (pc.coarse) {
-    CK(launch_seg_sum(pc, v, 1, C.coarse_rhs.as<double>(), s));
-    CK(launch_coarse_gemv<double>(pc.ao_inv.as<double>(), pc.n_o, C.coarse_rhs.as<double>(), C.coarse_x.as<double>(), s));
-    CK((launch_prolong<double, double>(C, pc, C.coarse_x.as<double>(), zG)));
+    CK(launch_seg_sum(pc, v, 1, W.crhs, s));
+    CK(launch_coarse_gemv<double>(pc.ao_inv.as<double>(), pc.n_o, W.crhs, W.cx, s));
+    CK((launch_prolong<double, double>(C, pc, W.cx, zG)));
     CK(launch_apply<double>(C, op, st, zG, v, t1, true));           // t1 = v - A z_G
   } else {
     CK(cudaMemsetAsync(zG, 0, sizeof(double) * n, s));
     CK(cudaMemcpyAsync(t1, v, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
   }
   CK(cudaMemsetAsync(zd, 0, sizeof(double) * n, s));
-  if (pc.precision == PNS_FP64) CKS((local_solve<double, double>(C, pc, pc.dual, t1, zd, 1)));
-  else if (pc.precision == PNS_FP32) CKS((local_solve<float, float>(C, pc, pc.dual, t1, zd, 1)));
-  else CKS((local_solve<__nv_bfloat16, float>(C, pc, pc.dual, t1, zd, 1)));
+  if (pc.precision == PNS_FP64) CKS((local_solve<double, double>(C, pc, pc.dual, t1, zd, 1, W)));
+  else if (pc.precision == PNS_FP32) CKS((local_solve<float, float>(C, pc, pc.dual, t1, zd, 1, W)));
+  else CKS((local_solve<__nv_bfloat16, float>(C, pc, pc.dual, t1, zd, 1, W)));
   CK(launch_apply<double>(C, op, st, zd, t1, t2, true));             // t2 = t1 - A z_d
   CK(cudaMemsetAsync(zp, 0, sizeof(double) * n, s));
-  if (pc.precision == PNS_FP64) CKS((local_solve<double, double>(C, pc, pc.prim, t2, zp, 0)));
-  else if (pc.precision == PNS_FP32) CKS((local_solve<float, float>(C, pc, pc.prim, t2, zp, 0)));
-  else CKS((local_solve<__nv_bfloat16, float>(C, pc, pc.prim, t2, zp, 0)));
+  if (pc.precision == PNS_FP64) CKS((local_solve<double, double>(C, pc, pc.prim, t2, zp, 0, W)));
+  else if (pc.precision == PNS_FP32) CKS((local_solve<float, float>(C, pc, pc.prim, t2, zp, 0, W)));
+  else CKS((local_solve<__nv_bfloat16, float>(C, pc, pc.prim, t2, zp, 0, W)));
   { pns::count_launch(); k_sum3<double><<<2048, 256, 0, s>>>(zG, zd, zp, z, n); }
   CK(cudaGetLastError());
   return PNS_OK;
 }
 
+namespace {
+
 int precond_apply(Ctx& C, Precond& pc, const double* v, double* z) {
   if (!pc.built) return fail(C, PNS_ERR_STATE, "preconditioner not built");
   if (pc.variant == PNS_BLOCK_SCHUR) return block_apply(C, pc, v, z);
-  return precond_apply_impl(C, pc, v, z);
+  ApplyScratch W;
+  W.zp = C.w0.as<double>();
+  W.zG = C.w1.as<double>();
+  W.t1 = C.w2.as<double>();
+  W.zd = C.w3.as<double>();
+  W.t2 = C.w4.as<double>();
+  W.pk = C.pk_x.p;
+  W.zpk = C.zpk.as<double>();
+  W.crhs = C.coarse_rhs.as<double>();
+  W.cx = C.coarse_x.as<double>();
+  W.timed = C.opt.timing != 0;
+  return precond_apply_with(C, pc, v, z, W);
 }
 
 // --------------------------------------------------------------------------- Krylov
@@ -910,7 +927,8 @@ int pns_setup(pns_ctx** out, int nz, int ny, int nx, const uint8_t* mask, const 
   else pns_default_options(&C.opt);
   if (C.opt.restart < 1 || C.opt.restart > 127 || C.opt.n_dilate < 0 || C.opt.n_tag < 1 || C.opt.precision < 0 ||
       C.opt.precision > 2 || C.opt.variant < 0 || C.opt.variant > 4 || C.opt.block_inner_its < 1 ||
-      C.opt.block_inner_its > 100 || !(C.opt.block_inner_tol > 0.0)) {
+      C.opt.block_inner_its > 100 || !(C.opt.block_inner_tol > 0.0) || C.opt.gj_tensor_cores < 0 ||
+      C.opt.gj_tensor_cores > 2) {
     delete ctx;
     return PNS_ERR_ARG;
   }
@@ -950,6 +968,16 @@ int pns_setup(pns_ctx** out, int nz, int ny, int nx, const uint8_t* mask, const 
   if (st != PNS_OK) {
     delete ctx;
     return st;
+  }
+  // device address of the fixed scratch array of pns_precond_apply_static, taken here (a call that may
+  // allocate) so that the allocation-free apply only reads it; a failure only disables that entry point
+  {
+    cudaError_t e = static_scratch_init(&C.static_scratch);
+    if (e != cudaSuccess) {
+      C.static_scratch = nullptr;
+      C.static_err = std::string("device address of the static scratch array: ") + cudaGetErrorString(e);
+      cudaGetLastError();
+    }
   }
   C.t_setup_ms = now_ms() - t0;
   *out = ctx;
@@ -997,6 +1025,8 @@ int pns_get_info(const pns_ctx* ctx, pns_info* info) {
                           &C.pc.ao_inv, &C.V, &C.Z, &C.w0, &C.w1, &C.w2, &C.w3, &C.w4, &C.pk_x, &C.pk_y};
   for (auto* p : bufs) bytes += p->bytes;
   info->device_bytes = bytes;
+  info->static_scratch_capacity = static_scratch_capacity();
+  info->static_apply_bytes = C.pc.built && C.pc.variant != PNS_BLOCK_SCHUR ? static_apply_bytes(C) : 0;
   return PNS_OK;
 }
 

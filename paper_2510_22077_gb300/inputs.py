@@ -705,3 +705,27 @@ def make_workload(kind: str, seed: int = 0, **kw) -> Workload:
     lab = label_pores(mask, target, per, method=kw.get("method", "window"), min_cells=kw.get("min_cells", min_cells),
                       max_cells=kw.get("max_cells", max_cells), split_cells=split)
     return Workload(kind, mask, lab.labels, per, dropped, lab.n_labels)
+
+
+# ----------------------------------------------------------------------------------------------
+# seeded synthetic velocity fields
+# ----------------------------------------------------------------------------------------------
+def synthetic_wind(shape, seed: int = 0, mean_x: float = 0.3, amplitude: float = 0.3,
+                   smooth: float = 2.0) -> np.ndarray:
+    """A seeded smooth random velocity in the full layout [u_x | u_y | (u_z) | p] of an image of
+    `shape` (nz, ny, nx): each velocity component is white noise smoothed by a Gaussian of width
+    `smooth` voxels (wrapping), scaled to unit standard deviation, times `amplitude`, plus `mean_x` on
+    u_x; the pressure block is zero.  It is a stand-in linearisation state ("wind") for tests of the
+    preconditioner builds; it holds no solver arithmetic, and entries that are not unknowns are left
+    to the caller to ignore or zero."""
+    nz, ny, nx = shape
+    dim = 2 if nz == 1 else 3
+    rng = np.random.default_rng(seed)
+    nc = nx * ny * nz
+    out = np.zeros((dim + 1) * nc)
+    for d in range(dim):
+        f = rng.standard_normal(shape)
+        f = ndimage.gaussian_filter(f, smooth, mode="wrap")
+        f = f / max(float(f.std()), 1e-300)
+        out[d * nc:(d + 1) * nc] = amplitude * f.ravel() + (mean_x if d == 0 else 0.0)
+    return out

@@ -66,7 +66,8 @@ class Info(ctypes.Structure):
                 ("n_pins", ctypes.c_int), ("n_dropped_labels", ctypes.c_int),
                 ("prim_unknowns_total", ctypes.c_longlong), ("dual_unknowns_total", ctypes.c_longlong),
                 ("prim_sum_n2", ctypes.c_double), ("dual_sum_n2", ctypes.c_double), ("max_block", ctypes.c_int),
-                ("device_bytes", ctypes.c_size_t)]
+                ("device_bytes", ctypes.c_size_t), ("static_scratch_capacity", ctypes.c_size_t),
+                ("static_apply_bytes", ctypes.c_size_t)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -185,7 +186,7 @@ class Solver:
         o.block_inner_its, o.block_inner_tol = int(block_inner_its), float(block_inner_tol)
         o.refine_steps = int(refine_steps)
         if gj_tensor_cores is not None:
-            o.gj_tensor_cores = int(bool(gj_tensor_cores))
+            o.gj_tensor_cores = int(gj_tensor_cores)
         s = stream if stream is not None else torch.cuda.current_stream()
         o.stream = ctypes.c_void_p(s.cuda_stream)
         self.stream = s

@@ -11,8 +11,6 @@ if ROOT not in sys.path:
 
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a) and the built libpns")
-    config.addinivalue_line("markers", "gpu_pending: a GPU test written before it could be run on a GPU; skipped "
-                                       "without one, selected explicitly (-m gpu_pending) until it joins the gpu set")
 
 
 @pytest.fixture(scope="session")
