@@ -14,7 +14,7 @@ LIB = os.path.join(OUT, "libpns.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall", "--expt-relaxed-constexpr"]
 SOURCES = ["pns_api.cu", "kernels_stencil.cu", "kernels_dense.cu", "kernels_coarse.cu", "kernels_krylov.cu", "maps.cpp",
-           "pns_static.cu", "kernels_block.cu", "kernels_gj_tc.cu"]
+           "pns_static.cu", "kernels_block.cu", "kernels_gj_tc.cu", "unet.cu"]
 
 
 def nvcc():

@@ -181,7 +181,7 @@ struct GjTc {
   ~GjTc();
   GjTc(const GjTc&) = delete;
   GjTc& operator=(const GjTc&) = delete;
-  cudaError_t setup(const BlockSet& B, float* mat, cudaStream_t s);
+  cudaError_t setup(const BlockSet& B, float* mat, cudaStream_t s, bool persistent);
   cudaError_t step(const BlockSet& B, float* mat, int k, int cnt, const int* d_order, const long long* d_pre2,
                    long long ntiles, const std::vector<int>& order, int* d_bad, cudaStream_t s);
 };

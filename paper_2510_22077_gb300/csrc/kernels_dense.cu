@@ -1300,11 +1300,12 @@ cudaError_t launch_gj_invert(const BlockSet& B, ST* mat, int* d_bad, cudaStream_
   }
   else
     cudaFuncSetAttribute(k_gj_update<ST, TBK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  // tensor_cores == 2: the update on the 5th-generation tensor cores (FP32 inverses only)
+  // tensor_cores 2 / 3: the update on the 5th-generation tensor cores (FP32 inverses only), persistent /
+  // one CTA per tile
   GjTc tc5;
-  const bool use_tc5 = std::is_same<ST, float>::value && tensor_cores == 2;
+  const bool use_tc5 = std::is_same<ST, float>::value && tensor_cores >= 2;
   if (use_tc5) {
-    if ((e = tc5.setup(B, (float*)mat, s)) != cudaSuccess) {
+    if ((e = tc5.setup(B, (float*)mat, s, tensor_cores == 2)) != cudaSuccess) {
       cudaFree(d_order); cudaFree(d_pre1); cudaFree(d_pre2);
       return e;
     }

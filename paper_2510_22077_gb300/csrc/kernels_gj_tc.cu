@@ -28,15 +28,19 @@
 #include <vector>
 
 #include "internal.h"
+#include "tc5.cuh"
 
 namespace pns {
 
 namespace {
 
+using namespace tc5;
+
 constexpr int TT = 128;          // tile edge (M = N) and panel width
 constexpr int KCH = 32;          // K chunk: 32 FP32 = one 128-byte swizzle row
 constexpr int NST = 2;           // operand stages
-constexpr long long WAIT_CYCLES = 2000000000LL;   // ~1 s at 2 GHz
+// tcgen05.mma kind::tf32, D FP32, A and B TF32 K-major, M = N = 128
+constexpr uint32_t IDESC_TF32 = idesc(FMT_TF32, TT, TT);
 
 struct __align__(1024) TcSmem {
   float c[4][TT][KCH];           // C tile, 4 boxes of 32 columns (64 KB)
@@ -48,96 +52,6 @@ struct __align__(1024) TcSmem {
   uint32_t tmem;
   int fail;
 };
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(unsigned long long* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ bool mbar_try(unsigned long long* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// bounded wait for the phase of the given parity to complete; false on timeout
-__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, uint32_t parity) {
-  if (mbar_try(bar, parity)) return true;
-  const long long t0 = clock64();
-  while (!mbar_try(bar, parity))
-    if (clock64() - t0 > WAIT_CYCLES) return false;
-  return true;
-}
-
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y,
-                                            unsigned long long* bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n" ::"r"(
-          smem_u32(dst)),
-      "l"(map), "r"(x), "r"(y), "r"(smem_u32(bar))
-      : "memory");
-}
-__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, int x, int y, const void* src) {
-  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];\n" ::"l"(map), "r"(x),
-               "r"(y), "r"(smem_u32(src))
-               : "memory");
-}
-
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
-
-// Shared-memory matrix descriptor of a K-major operand tile in the 128-byte swizzle layout: rows of
-// 128 bytes, 8-row swizzle atoms 1024 bytes apart (stride byte offset), descriptor version 1, layout
-// type 2 (SWIZZLE_128B).  The tile base is 1024-byte aligned; the K offset inside the atom is added to
-// the start address.
-__device__ __forceinline__ uint64_t sw128_desc(const void* tile, uint32_t kbyte) {
-  const uint32_t a = smem_u32(tile) + kbyte;
-  uint64_t d = (uint64_t)((a >> 4) & 0x3FFFu);
-  d |= (uint64_t)1 << 16;                  // leading byte offset (unused by swizzled K-major layouts)
-  d |= (uint64_t)(1024 >> 4) << 32;        // stride byte offset
-  d |= (uint64_t)1 << 46;                  // descriptor version
-  d |= (uint64_t)2 << 61;                  // SWIZZLE_128B
-  return d;
-}
-
-// Instruction descriptor of tcgen05.mma kind::tf32: D FP32, A and B TF32, both K-major, N = 128, M = 128.
-constexpr uint32_t IDESC_TF32 = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(TT >> 3) << 17) |
-                                ((uint32_t)(TT >> 4) << 24);
-
-__device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
-      "l"(adesc), "l"(bdesc), "r"(IDESC_TF32), "r"(accumulate)
-      : "memory");
-}
-__device__ __forceinline__ void mma_commit(unsigned long long* bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(smem_u32(bar))
-               : "memory");
-}
-
-// 32 TMEM lanes x 32 columns of 32 bits: lane (32 w + t) of warp w goes to thread t
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
-  uint32_t r[32];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];\n"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
-        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
-        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-#pragma unroll
-  for (int q = 0; q < 32; ++q) v[q] = __uint_as_float(r[q]);
-}
 
 __device__ __forceinline__ int find_blk(const long long* __restrict__ off, int nb, long long t) {
   int lo = 0, hi = nb - 1;
@@ -282,9 +196,9 @@ __global__ void __launch_bounds__(128, 1) k_gj_update_tc(int k, int cnt, const i
         const uint32_t kb = kk * 32;
         const uint64_t ah = sw128_desc(&S.a_hi[st][0][0], kb), al = sw128_desc(&S.a_lo[st][0][0], kb);
         const uint64_t bh = sw128_desc(&S.b_hi[st][0][0], kb), bl = sw128_desc(&S.b_lo[st][0][0], kb);
-        mma_tf32(tmem, ah, bh, (c | kk) != 0);
-        mma_tf32(tmem, ah, bl, 1);
-        mma_tf32(tmem, al, bh, 1);
+        mma_tf32(tmem, ah, bh, IDESC_TF32, (c | kk) != 0);
+        mma_tf32(tmem, ah, bl, IDESC_TF32, 1);
+        mma_tf32(tmem, al, bh, IDESC_TF32, 1);
       }
       mma_commit(&S.empty[st]);
     }
@@ -336,6 +250,197 @@ __global__ void __launch_bounds__(128, 1) k_gj_update_tc(int k, int cnt, const i
   }
 }
 
+// --------------------------------------------------------------------------------- persistent update
+// The same update as k_gj_update_tc, persistent and warp-specialised so that the load, the tensor-core
+// product and the write-back of consecutive tiles overlap: one CTA per SM walks the tiles
+// blockIdx.x, blockIdx.x + gridDim.x, ...; warp 0 (one thread) streams the operand chunks through the two
+// stages and, once the previous tile's write-back has read the C buffer, the next C tile; warp 1 (one
+// thread) issues the MMAs of each tile into one of two 128-column TMEM accumulators; warps 2-5 read an
+// accumulator back (warp w owns TMEM lanes 32 (w % 4) ..), update the C tile in shared memory and store
+// it with TMA.  A wait that times out raises the CTA's abort flag, which ends every role's loop.
+struct __align__(1024) TcpSmem {
+  float c[4][TT][KCH];           // C tile (one buffer, 64 KB)
+  float a_hi[NST][TT][KCH];
+  float a_lo[NST][TT][KCH];
+  float b_hi[NST][TT][KCH];
+  float b_lo[NST][TT][KCH];
+  unsigned long long full[NST], empty[NST], c_full, c_empty, acc_full[2], acc_empty[2];
+  uint32_t tmem;
+  volatile int abort;
+};
+
+__device__ __forceinline__ bool wait_or_abort(unsigned long long* bar, uint32_t parity, volatile int* abort) {
+  if (mbar_try(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_try(bar, parity)) {
+    if (*abort) return false;
+    if (clock64() - t0 > WAIT_CYCLES) {
+      *abort = 1;
+      return false;
+    }
+  }
+  return true;
+}
+
+__device__ __forceinline__ void tile_of(long long w, int k, int cnt, const int* __restrict__ order,
+                                        const long long* __restrict__ pre2, const int* __restrict__ bn,
+                                        const long long* __restrict__ ioff, int& b, int& i0, int& j0, int& rowA,
+                                        int& rowB) {
+  const int s = find_blk(pre2, cnt, w);
+  b = order[s];
+  const int n = bn[b];
+  const int T = (n + TT - 1) / TT;
+  const long long loc = w - pre2[s];
+  i0 = skip_k((int)(loc / (T - 1)), k) * TT;
+  j0 = skip_k((int)(loc % (T - 1)), k) * TT;
+  rowA = (int)(ioff[b] + i0);
+  rowB = (int)(ioff[b] + j0);
+}
+
+__global__ void __launch_bounds__(192, 1) k_gj_update_tcp(int k, int cnt, long long ntiles,
+                                                          const int* __restrict__ order,
+                                                          const long long* __restrict__ pre2,
+                                                          const int* __restrict__ bn,
+                                                          const long long* __restrict__ ioff,
+                                                          const CUtensorMap* __restrict__ mat_maps,
+                                                          const __grid_constant__ CUtensorMap pa_hi,
+                                                          const __grid_constant__ CUtensorMap pa_lo,
+                                                          const __grid_constant__ CUtensorMap pb_hi,
+                                                          const __grid_constant__ CUtensorMap pb_lo,
+                                                          int* __restrict__ flag) {
+  extern __shared__ unsigned char smraw[];
+  TcpSmem& S = *reinterpret_cast<TcpSmem*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~(uintptr_t)1023);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int st = 0; st < NST; ++st) {
+      mbar_init(&S.full[st], 1);
+      mbar_init(&S.empty[st], 1);
+    }
+    mbar_init(&S.c_full, 1);
+    mbar_init(&S.c_empty, 1);
+    for (int q = 0; q < 2; ++q) {
+      mbar_init(&S.acc_full[q], 1);
+      mbar_init(&S.acc_empty[q], 128);
+    }
+    S.abort = 0;
+    fence_mbar_init();
+  }
+  if (warp == 0) tmem_alloc(&S.tmem, 2 * TT);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = S.tmem;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // producer
+      long long q = 0;
+      int it = 0;
+      for (long long w = blockIdx.x; w < ntiles && !S.abort; w += gridDim.x, ++it) {
+        int b, i0, j0, rowA, rowB;
+        tile_of(w, k, cnt, order, pre2, bn, ioff, b, i0, j0, rowA, rowB);
+        for (int c = 0; c < TT / KCH; ++c, ++q) {
+          const int st = (int)(q % NST);
+          if (q >= NST && !wait_or_abort(&S.empty[st], (uint32_t)(((q - NST) / NST) & 1), &S.abort)) break;
+          mbar_expect_tx(&S.full[st], 4u * TT * KCH * 4u);
+          tma_load_2d(&S.a_hi[st][0][0], &pa_hi, c * KCH, rowA, &S.full[st]);
+          tma_load_2d(&S.a_lo[st][0][0], &pa_lo, c * KCH, rowA, &S.full[st]);
+          tma_load_2d(&S.b_hi[st][0][0], &pb_hi, c * KCH, rowB, &S.full[st]);
+          tma_load_2d(&S.b_lo[st][0][0], &pb_lo, c * KCH, rowB, &S.full[st]);
+        }
+        if (S.abort) break;
+        if (it > 0 && !wait_or_abort(&S.c_empty, (uint32_t)((it - 1) & 1), &S.abort)) break;
+        mbar_expect_tx(&S.c_full, (uint32_t)sizeof(S.c));
+        for (int qq = 0; qq < 4; ++qq) tma_load_2d(&S.c[qq][0][0], mat_maps + b, j0 + qq * KCH, i0, &S.c_full);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // MMA issuer
+      long long q = 0;
+      int it = 0;
+      for (long long w = blockIdx.x; w < ntiles && !S.abort; w += gridDim.x, ++it) {
+        const int ab = it & 1;
+        if (it >= 2 && !wait_or_abort(&S.acc_empty[ab], (uint32_t)(((it - 2) >> 1) & 1), &S.abort)) break;
+        tc_fence_after();
+        const uint32_t acc = tmem + (uint32_t)(ab * TT);
+        bool ok = true;
+        for (int c = 0; c < TT / KCH; ++c, ++q) {
+          const int st = (int)(q % NST);
+          if (!wait_or_abort(&S.full[st], (uint32_t)((q / NST) & 1), &S.abort)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+#pragma unroll
+          for (int kk = 0; kk < KCH / 8; ++kk) {
+            const uint32_t kb = kk * 32;
+            const uint64_t ah = sw128_desc(&S.a_hi[st][0][0], kb), al = sw128_desc(&S.a_lo[st][0][0], kb);
+            const uint64_t bh = sw128_desc(&S.b_hi[st][0][0], kb), bl = sw128_desc(&S.b_lo[st][0][0], kb);
+            mma_tf32(acc, ah, bh, IDESC_TF32, (c | kk) != 0);
+            mma_tf32(acc, ah, bl, IDESC_TF32, 1);
+            mma_tf32(acc, al, bh, IDESC_TF32, 1);
+          }
+          mma_commit(&S.empty[st]);
+        }
+        if (!ok) break;
+        mma_commit(&S.acc_full[ab]);
+      }
+    }
+  } else {
+    // epilogue: warps 2..5, TMEM lane quarter warp % 4
+    const int quarter = warp & 3;
+    const int r = quarter * 32 + lane;
+    int it = 0;
+    for (long long w = blockIdx.x; w < ntiles; w += gridDim.x, ++it) {
+      int b, i0, j0, rowA, rowB;
+      tile_of(w, k, cnt, order, pre2, bn, ioff, b, i0, j0, rowA, rowB);
+      const int ab = it & 1;
+      const bool ok = wait_or_abort(&S.acc_full[ab], (uint32_t)((it >> 1) & 1), &S.abort) &&
+                      wait_or_abort(&S.c_full, (uint32_t)(it & 1), &S.abort);
+      // all 128 epilogue threads take the same branch: a timeout anywhere sets the abort flag first
+      asm volatile("bar.sync 1, 128;\n" ::: "memory");
+      if (!ok || S.abort) break;
+      tc_fence_after();
+      const uint32_t acc = tmem + (uint32_t)(ab * TT) + ((uint32_t)(quarter * 32) << 16);
+#pragma unroll 1
+      for (int qq = 0; qq < 4; ++qq) {
+        float v[32];
+        tmem_ld32(acc + (uint32_t)(qq * KCH), v);
+        float* crow = &S.c[qq][r][0];
+#pragma unroll
+        for (int ch = 0; ch < 8; ++ch) {
+          float4* p = reinterpret_cast<float4*>(crow + ((ch ^ (r & 7)) * 4));
+          float4 x = *p;
+          x.x -= v[ch * 4 + 0];
+          x.y -= v[ch * 4 + 1];
+          x.z -= v[ch * 4 + 2];
+          x.w -= v[ch * 4 + 3];
+          *p = x;
+        }
+      }
+      tc_fence_before();
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(&S.acc_empty[ab])) : "memory");
+      fence_async_smem();
+      asm volatile("bar.sync 1, 128;\n" ::: "memory");
+      if (warp == 2 && lane == 0) {
+        for (int qq = 0; qq < 4; ++qq) tma_store_2d(mat_maps + b, j0 + qq * KCH, i0, &S.c[qq][0][0]);
+        asm volatile("cp.async.bulk.commit_group;\n" ::: "memory");
+        asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory");
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(&S.c_empty)) : "memory");
+      }
+    }
+    if (warp == 2 && lane == 0) asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (threadIdx.x == 0 && S.abort) atomicOr(flag, 2);
+  if (warp == 0) {
+    tc_fence_after();
+    tmem_free(tmem, 2 * TT);
+  }
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
   if (!fn) {
@@ -370,6 +475,8 @@ struct GjTcImpl {
   long long rows = 0;
   CUtensorMap pa_hi, pa_lo, pb_hi, pb_lo;
   long long* d_preT = nullptr;
+  int sms = 148;
+  bool persistent = true;
   ~GjTcImpl() {
     if (panels) cudaFree(panels);
     if (d_maps) cudaFree(d_maps);
@@ -380,10 +487,11 @@ struct GjTcImpl {
 GjTc::GjTc() : impl(nullptr) {}
 GjTc::~GjTc() { delete impl; }
 
-cudaError_t GjTc::setup(const BlockSet& B, float* mat, cudaStream_t s) {
+cudaError_t GjTc::setup(const BlockSet& B, float* mat, cudaStream_t s, bool persistent) {
   delete impl;
   impl = new GjTcImpl;
   GjTcImpl& I = *impl;
+  I.persistent = persistent;
   I.rows = std::max<long long>(B.n_total, 1);
   cudaError_t e = cudaMalloc(&I.panels, sizeof(float) * (size_t)I.rows * TT * 4);
   if (e != cudaSuccess) return e;
@@ -407,8 +515,14 @@ cudaError_t GjTc::setup(const BlockSet& B, float* mat, cudaStream_t s) {
     e = cudaFuncSetAttribute(k_gj_update_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(sizeof(TcSmem) + 1024));
     if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_gj_update_tcp, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(sizeof(TcpSmem) + 1024));
+    if (e != cudaSuccess) return e;
     attr = true;
   }
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&impl->sms, cudaDevAttrMultiProcessorCount, dev);
   return cudaSuccess;
 }
 
@@ -427,7 +541,14 @@ cudaError_t GjTc::step(const BlockSet& B, float* mat, int k, int cnt, const int*
                                                    I.panels + 2 * (size_t)I.rows * TT,
                                                    I.panels + 3 * (size_t)I.rows * TT);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  if (ntiles > 0) {
+  if (ntiles > 0 && I.persistent) {
+    pns::count_launch();
+    const unsigned grid = (unsigned)std::min<long long>(ntiles, I.sms);
+    k_gj_update_tcp<<<grid, 192, sizeof(TcpSmem) + 1024, s>>>(k, cnt, ntiles, d_order, d_pre2, B.d_n.as<int>(),
+                                                               B.d_ioff.as<long long>(), I.d_maps, I.pa_hi, I.pa_lo,
+                                                               I.pb_hi, I.pb_lo, d_bad);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  } else if (ntiles > 0) {
     pns::count_launch();
     k_gj_update_tc<<<(unsigned)ntiles, 128, sizeof(TcSmem) + 1024, s>>>(
         k, cnt, d_order, d_pre2, B.d_n.as<int>(), B.d_ioff.as<long long>(), I.d_maps, I.pa_hi, I.pa_lo, I.pb_hi,

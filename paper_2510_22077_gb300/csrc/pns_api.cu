@@ -911,7 +911,7 @@ void pns_default_options(pns_options* o) {
   o->stream = nullptr;
   o->block_inner_its = 20;
   o->block_inner_tol = 1e-2;
-  o->gj_tensor_cores = 0;
+  o->gj_tensor_cores = 2;
 }
 
 int pns_setup(pns_ctx** out, int nz, int ny, int nx, const uint8_t* mask, const int32_t* labels, double rho,
@@ -928,7 +928,7 @@ int pns_setup(pns_ctx** out, int nz, int ny, int nx, const uint8_t* mask, const 
   if (C.opt.restart < 1 || C.opt.restart > 127 || C.opt.n_dilate < 0 || C.opt.n_tag < 1 || C.opt.precision < 0 ||
       C.opt.precision > 2 || C.opt.variant < 0 || C.opt.variant > 4 || C.opt.block_inner_its < 1 ||
       C.opt.block_inner_its > 100 || !(C.opt.block_inner_tol > 0.0) || C.opt.gj_tensor_cores < 0 ||
-      C.opt.gj_tensor_cores > 2) {
+      C.opt.gj_tensor_cores > 3) {
     delete ctx;
     return PNS_ERR_ARG;
   }

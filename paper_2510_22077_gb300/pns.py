@@ -308,3 +308,170 @@ class Solver:
                                              P(dual_count), P(pins)), "pns_export_maps")
         return {"cell_prim": cell_prim, "cell_iface": cell_iface, "face_class": face_class.reshape(dim, nc),
                 "tags": tags.reshape(dim, nc).astype(bool), "dual_count": dual_count, "pins": pins[:n_pins]}
+
+
+# ------------------------------------------------------------------------------------ learned initial guess
+def unet_param_names(levels):
+    """Names of the flat parameter vector of pns_unet (include/pns_unet.h), in its order: each
+    convolution's weight then bias, enc0.0 .. enc{L-1}.1, dec{L-2}.0 .. dec0.1, head."""
+    names = []
+    for l in range(levels):
+        names += [f"enc{l}.0", f"enc{l}.1"]
+    for l in range(levels - 2, -1, -1):
+        names += [f"dec{l}.0", f"dec{l}.1"]
+    names.append("head")
+    out = []
+    for n in names:
+        out += [n + ".w", n + ".b"]
+    return out
+
+
+_UNET_SIG = False
+
+
+def _load_unet():
+    global _UNET_SIG
+    lib = load()
+    if not _UNET_SIG:
+        P, I, D, F, V, LL = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_float, None, ctypes.c_longlong
+        sig = {
+            "pns_unet_create": (I, [ctypes.POINTER(P), I, P, I, I, I, I, I, I, ctypes.c_uint64, P]),
+            "pns_unet_destroy": (V, [P]),
+            "pns_unet_last_error": (ctypes.c_char_p, [P]),
+            "pns_unet_num_params": (LL, [P]),
+            "pns_unet_set_params": (I, [P, P]),
+            "pns_unet_get_params": (I, [P, P]),
+            "pns_unet_get_grads": (I, [P, P]),
+            "pns_unet_forward": (I, [P, P, I, I, I, I, P]),
+            "pns_unet_backward": (I, [P, P]),
+            "pns_unet_mse": (I, [P, P, P, P, I, I, I, I, P, ctypes.POINTER(D)]),
+            "pns_unet_adam": (I, [P, F, F, F, F]),
+            "pns_unet_train_step": (I, [P, P, P, P, I, I, I, I, F, ctypes.POINTER(D)]),
+            "pns_unet_features": (I, [P, P, P, D, I, I, I, P, I, P]),
+            "pns_unet_targets": (I, [P, P, P, P, D, D, I, I, I, P, P, I]),
+            "pns_unet_proposal": (I, [P, P, I, P, D, D, I, I, I, P]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _UNET_SIG = True
+    return lib
+
+
+def _fptr(t, dtype=None):
+    import torch
+    if t is None:
+        return None
+    want = dtype or torch.float32
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == want and t.is_contiguous()):
+        raise TypeError(f"expected a contiguous {want} CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class UNet:
+    """The 3D U-Net of the learned Newton initial guess (include/pns_unet.h): BF16 tensor-core kernels,
+    FP32 master weights, Adam.  Tensors are float32 CUDA tensors of shape (N, C, D, H, W)."""
+
+    def __init__(self, channels=(16, 32, 64, 64), in_ch=6, out_ch=4, batch=1, shape=(64, 64, 64), seed=0,
+                 stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("libpns needs a CUDA device")
+        self.lib = _load_unet()
+        self.channels, self.in_ch, self.out_ch = tuple(channels), in_ch, out_ch
+        self.levels = len(channels)
+        s = stream if stream is not None else torch.cuda.current_stream()
+        self.stream = s
+        ch = (ctypes.c_int * self.levels)(*channels)
+        h = ctypes.c_void_p()
+        nz, ny, nx = shape
+        rc = self.lib.pns_unet_create(ctypes.byref(h), self.levels, ctypes.cast(ch, ctypes.c_void_p), in_ch, out_ch,
+                                      batch, nz, ny, nx, seed, ctypes.c_void_p(s.cuda_stream))
+        if rc != 0:
+            raise PnsError(rc, "pns_unet_create failed (bad sizes, or out of device memory)")
+        self.h = h
+
+    def __del__(self):
+        h = getattr(self, "h", None)
+        if h:
+            self.lib.pns_unet_destroy(h)
+            self.h = None
+
+    def close(self):
+        self.__del__()
+
+    def _check(self, rc, what):
+        if rc != 0:
+            raise PnsError(rc, f"{what}: {self.lib.pns_unet_last_error(self.h).decode()}")
+
+    def num_params(self):
+        return int(self.lib.pns_unet_num_params(self.h))
+
+    def set_params(self, flat):
+        a = np.ascontiguousarray(flat, dtype=np.float32)
+        if a.size != self.num_params():
+            raise ValueError("wrong parameter count")
+        self._check(self.lib.pns_unet_set_params(self.h, a.ctypes.data_as(ctypes.c_void_p)), "pns_unet_set_params")
+
+    def get_params(self):
+        a = np.zeros(self.num_params(), np.float32)
+        self._check(self.lib.pns_unet_get_params(self.h, a.ctypes.data_as(ctypes.c_void_p)), "pns_unet_get_params")
+        return a
+
+    def get_grads(self):
+        a = np.zeros(self.num_params(), np.float32)
+        self._check(self.lib.pns_unet_get_grads(self.h, a.ctypes.data_as(ctypes.c_void_p)), "pns_unet_get_grads")
+        return a
+
+    def forward(self, x, out=None):
+        import torch
+        n, c, d, hh, w = x.shape
+        out = torch.empty((n, self.out_ch, d, hh, w), dtype=torch.float32, device="cuda") if out is None else out
+        self._check(self.lib.pns_unet_forward(self.h, _fptr(x), n, d, hh, w, _fptr(out)), "pns_unet_forward")
+        return out
+
+    def backward(self, gout):
+        self._check(self.lib.pns_unet_backward(self.h, _fptr(gout)), "pns_unet_backward")
+
+    def mse(self, out, target, weight):
+        import torch
+        n, c, d, hh, w = out.shape
+        g = torch.empty_like(out)
+        loss = ctypes.c_double()
+        self._check(self.lib.pns_unet_mse(self.h, _fptr(out), _fptr(target), _fptr(weight), n, d, hh, w, _fptr(g),
+                                          ctypes.byref(loss)), "pns_unet_mse")
+        return loss.value, g
+
+    def adam(self, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
+        self._check(self.lib.pns_unet_adam(self.h, lr, b1, b2, eps), "pns_unet_adam")
+
+    def train_step(self, x, target, weight, lr=1e-3):
+        n, c, d, hh, w = x.shape
+        loss = ctypes.c_double()
+        self._check(self.lib.pns_unet_train_step(self.h, _fptr(x), _fptr(target), _fptr(weight), n, d, hh, w, lr,
+                                                 ctypes.byref(loss)), "pns_unet_train_step")
+        return loss.value
+
+    def features(self, mask_u8, x_stokes, re, x, b=0):
+        """Encode one image (device uint8 mask, FP64 full-layout Stokes solution) into batch entry b of x;
+        returns the scales (U, P)."""
+        import torch
+        nz, ny, nx = mask_u8.shape
+        sc = (ctypes.c_double * 2)()
+        self._check(self.lib.pns_unet_features(self.h, _fptr(mask_u8, torch.uint8), _ptr(x_stokes), float(re), nz, ny,
+                                               nx, _fptr(x), b, ctypes.cast(sc, ctypes.c_void_p)), "pns_unet_features")
+        return sc[0], sc[1]
+
+    def targets(self, mask_u8, x_ns, x_stokes, scales, t, w=None, b=0):
+        import torch
+        nz, ny, nx = mask_u8.shape
+        self._check(self.lib.pns_unet_targets(self.h, _fptr(mask_u8, torch.uint8), _ptr(x_ns), _ptr(x_stokes),
+                                              float(scales[0]), float(scales[1]), nz, ny, nx, _fptr(t),
+                                              _fptr(w) if w is not None else None, b), "pns_unet_targets")
+
+    def proposal(self, out, x_stokes, scales, x_out, b=0):
+        nz, ny, nx = out.shape[2:]
+        self._check(self.lib.pns_unet_proposal(self.h, _fptr(out), b, _ptr(x_stokes), float(scales[0]),
+                                               float(scales[1]), nz, ny, nx, _ptr(x_out)), "pns_unet_proposal")
+        return x_out

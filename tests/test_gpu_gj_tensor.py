@@ -17,7 +17,7 @@ pytestmark = pytest.mark.gpu
 
 
 @pytest.mark.parametrize("kind,kw,variant", [("disks64", {}, "gplmm"), ("spheres", {"n": 32}, "aplmm_s"),
-                                             ("spheres", {"n": 40}, "gplmm")])
+                                             ("spheres", {"n": 48}, "aplmm_ns")])
 def test_tensor_core_update_matches_oracle_and_fma(kind, kw, variant):
     w = inputs.make_workload(kind, seed=0, **kw)
     mu = 3.87 if kind == "disks64" else inputs.mu_kozeny_carman(w.mask, 1.0)
