@@ -58,6 +58,15 @@ def parse(argv=None):
                          "(default: the library's)")
     ap.add_argument("--jac-only", action="store_true",
                     help="time only the FP64 Jacobian apply (pns_setup + pns_jacobian_apply; no preconditioner)")
+    ap.add_argument("--learned", action="store_true",
+                    help="the learned-initial-guess experiment instead of the main line: solver-generated samples, "
+                         "U-Net training on the GPU, Newton from the Stokes vs the guarded learned start on "
+                         "held-out images")
+    ap.add_argument("--samples", type=int, default=256)
+    ap.add_argument("--epochs", type=int, default=30)
+    ap.add_argument("--sample-n", type=int, default=64)
+    ap.add_argument("--heldout", default="64:9000-9007,96:9000-9001",
+                    help="held-out images as size:first-last seed ranges")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--precisions", default="fp64,fp32,bf16",
@@ -414,6 +423,65 @@ def compare_precisions(args):
     return out
 
 
+def run_learned(args):
+    """The learned Newton initial guess (BASELINE config 5 at reduced scale, stated in the line): samples
+    generated by the solver, the U-Net trained on the GPU, then on held-out images Newton from the Stokes
+    solution and from the guarded learned start, each timed with CUDA events."""
+    import numpy as np
+    import torch
+    from paper_2510_22077_gb300 import learned, pns
+    t0 = time.time()
+    n = args.sample_n
+    net = pns.UNet(channels=(16, 32, 64, 64), in_ch=6, out_ch=4, batch=4, shape=(n, n, n), seed=args.seed)
+    data = learned.Dataset(net, args.samples, n=n, seed0=1000)
+    t_data = time.time() - t0
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(net.stream)
+    hist = learned.train(net, data, epochs=args.epochs, batch=4, lr=1e-3, seed=args.seed)
+    e1.record(net.stream)
+    torch.cuda.synchronize()
+    t_train = e0.elapsed_time(e1) / 1e3
+    evals = []
+    for spec in args.heldout.split(","):
+        size, rng_ = spec.split(":")
+        lo, hi = (int(v) for v in rng_.split("-"))
+        for seed in range(lo, hi + 1):
+            kind = "spheres" if seed % 2 == 0 else "grf"
+            w, phi = learned._image(kind, seed, int(size))
+            re = float(np.random.default_rng(seed + 7).uniform(1.0, 100.0))
+            if int(size) != n:
+                # the network is fully convolutional: run it at the held-out size
+                net_eval = pns.UNet(channels=(16, 32, 64, 64), in_ch=6, out_ch=4, batch=1,
+                                    shape=w.mask.shape, seed=0)
+                net_eval.set_params(net.get_params())
+            else:
+                net_eval = net
+            try:
+                r = learned.compare_on(w, re, net_eval)
+            except Exception as ex:   # recorded
+                r = {"error": f"{type(ex).__name__}: {ex}"[:200]}
+            evals.append({"size": int(size), "seed": seed, "kind": kind, "phi": phi, "re": re, **r})
+            if net_eval is not net:
+                net_eval.close()
+    ok = [e for e in evals if "stokes" in e and e["stokes"]["status"] == "PNS_OK" and e["learned"]["status"] == "PNS_OK"]
+    line = {"metric": "learned Newton initial guess: Newton iterations and time to 1e-8, Stokes start vs learned start",
+            "unit": "ms", "data": "synthetic (seeded sphere packs and Gaussian fields)",
+            "config": {"workload": f"3D U-Net (16/32/64/64, BF16, FP32 master, Adam) trained on {data.m} solver-generated "
+                                   f"{n}^3 samples ({data.skipped} images skipped: failed solves), {args.epochs} epochs; "
+                                   f"held-out {args.heldout}", "samples": data.m, "skipped": data.skipped,
+                       "re_range": [1, 100]},
+            "seconds": {"samples": t_data, "train": t_train}, "loss_per_epoch": hist,
+            "heldout": evals,
+            "summary": {"images": len(ok),
+                        "newton_its_stokes": float(np.mean([e["stokes"]["newton_its"] for e in ok])) if ok else None,
+                        "newton_its_learned": float(np.mean([e["learned"]["newton_its"] for e in ok])) if ok else None,
+                        "ms_stokes": float(np.mean([e["stokes"]["ms"] for e in ok])) if ok else None,
+                        "ms_learned": float(np.mean([e["learned"]["ms"] for e in ok])) if ok else None,
+                        "network_used": int(sum(e["learned"]["used_network"] for e in ok))}}
+    print(json.dumps(line), flush=True)
+    net.close()
+
+
 # ---------------------------------------------------------------------------------------- main
 def main():
     if len(sys.argv) > 2 and sys.argv[1] == "--oracle-worker":
@@ -424,6 +492,8 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.learned:
+        return run_learned(args)
     import torch
     dist = None
     if world > 1:

@@ -215,6 +215,26 @@ int pns_precond_apply(pns_ctx* ctx, const double* v, double* z);
  * BLOCK_SCHUR variant. */
 int pns_precond_apply_static(pns_ctx* ctx, const double* v, double* z);
 
+/* Shapes of the batched local solves (Eq. 25: M_p and M_d applied as one persistent launch per block set).
+ * The blocks are binned by size n: bin 0 n <= 64, 1 n <= 256, 2 n <= 1024, 3 n <= 4096, 4 n <= 16384,
+ * 5 larger; each bin uses one of PNS_TUNE_CONFIGS shapes (lanes per matrix row, rows per work item):
+ * 0 (8, 32), 1 (8, 128), 2 (16, 32), 3 (16, 128), 4 (32, 16), 5 (32, 64).  Default table {1, 3, 5, 5, 5, 5}.
+ * The paper has no counterpart: this is how this library schedules the paper's batched local solves. */
+#define PNS_TUNE_BINS 6
+#define PNS_TUNE_CONFIGS 6
+
+/* Time every shape on every size bin of the built preconditioner's primary and dual blocks (CUDA events,
+ * best of five launches after one warm-up, the two block sets summed) and adopt the fastest per bin.
+ * table (HOST, PNS_TUNE_BINS ints, may be NULL) receives the chosen config ids; ms (HOST,
+ * PNS_TUNE_BINS * PNS_TUNE_CONFIGS doubles, may be NULL) the times, ms[bin * PNS_TUNE_CONFIGS + config],
+ * 0 for a bin with no block.  Allocates scratch for the duration of the call.  Synchronises.
+ * PNS_ERR_STATE without a built PLMM-family preconditioner. */
+int pns_autotune(pns_ctx* ctx, int* table, double* ms);
+
+/* Adopt a tuning table (PNS_TUNE_BINS config ids, HOST), e.g. one saved from pns_autotune on the same
+ * kind of GPU.  PNS_ERR_ARG for an id out of range. */
+int pns_set_tuning(pns_ctx* ctx, const int* table);
+
 /* Newton-FGMRES (Sec. 8).  x: device, full layout; initial guess on input, solution on output.
  * x_prev: previous time level (transient) or NULL.  Builds the preconditioner at the initial
  * guess if none is built.  st may be NULL.  Synchronises.  PNS_ERR_NOT_CONVERGED if max_newton is

@@ -48,10 +48,22 @@ struct BlockSet {
   DevBuf idx;                    // int32 full indices, concatenated
   DevBuf d_n, d_ld, d_ioff, d_moff;
   DevBuf mat;                    // inverse storage (type depends on precision)
-  // GEMV work list: (block, first row, row count)
-  int nitems = 0;
-  DevBuf items;                  // int4
+  // binned work list of the persistent GEMV: (block, first row, row count, lanes per row), largest blocks
+  // first; built from the context's tuning table (build_gemv_items)
+  int nitems_p = 0;
+  DevBuf items_p;                // int4
+  DevBuf counter;                // int: next item of the running launch
 };
+
+// Size bins and shapes of the persistent local GEMV (pns_autotune / pns_set_tuning of pns.h).
+constexpr int TUNE_BINS = 6;     // n <= 64, 256, 1024, 4096, 16384, larger
+constexpr int TUNE_CONFIGS = 6;  // (lanes per row, rows per item)
+inline int tune_bin(int n) {
+  return n <= 64 ? 0 : n <= 256 ? 1 : n <= 1024 ? 2 : n <= 4096 ? 3 : n <= 16384 ? 4 : 5;
+}
+constexpr int TUNE_LANES[TUNE_CONFIGS] = {8, 8, 16, 16, 32, 32};
+constexpr int TUNE_ROWS[TUNE_CONFIGS] = {32, 128, 32, 128, 16, 64};
+constexpr int TUNE_DEFAULT[TUNE_BINS] = {1, 3, 5, 5, 5, 5};
 
 // Block-triangular Schur comparator (variant PNS_BLOCK_SCHUR): pore blocks of F and L = B2 D^-1 B1 for
 // block Jacobi, D = diag(F), and the workspace of its inner GMRES.
@@ -130,6 +142,8 @@ struct Ctx {
   double t_setup_ms = 0;
   double t_mg_ms = 0, t_ml_ms = 0;
   GjTimer gj;                    // update-kernel timing of the local-inverse builds (timing == 1)
+  int tune[TUNE_BINS] = {TUNE_DEFAULT[0], TUNE_DEFAULT[1], TUNE_DEFAULT[2], TUNE_DEFAULT[3], TUNE_DEFAULT[4],
+                         TUNE_DEFAULT[5]};   // config of each size bin of the persistent local GEMV
   void* static_scratch = nullptr;  // device address of the fixed scratch array of pns_precond_apply_static
   std::string static_err;        // why that address could not be taken at set-up ("" if it was)
 };
@@ -197,6 +211,8 @@ cudaError_t launch_block_mm(const BlockSet& B, const ST* mat, const double* rhs,
 template <typename ST, typename PT>
 cudaError_t launch_local_solve_refined(const Ctx& C, const BlockSet& B, int op, const double* state, const ST* mat,
                                        const double* t, double* z, PT* pk_x, double* zp, int add, cudaStream_t s);
+template <typename ST, typename PT>
+cudaError_t launch_local_gemv_p(const BlockSet& B, const ST* mat, const PT* pk, double* z, int mode, cudaStream_t s);
 template <typename ST, typename PT>
 cudaError_t launch_local_solve(const BlockSet& B, const ST* mat, const double* t, double* z, PT* pk_x, int add,
                                cudaStream_t s);

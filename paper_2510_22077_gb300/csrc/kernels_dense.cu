@@ -774,34 +774,54 @@ __device__ __forceinline__ float dot16(const __nv_bfloat16* a, const float* x) {
 }
 template <typename ST> struct VecW { static constexpr int n = 16 / sizeof(ST); };
 
-// One warp per row; item = (block, first row, rows).  Output (FP64) by `mode`: 0 z[idx[row]] = y,
-// 1 z[idx[row]] += y (atomic: overlapping dual grids), 2 packed zp[row] = y, 3 packed zp[row] += y.
-// The dot products run in the packed type PT (FP32 for the FP32/BF16 inverses): per-lane partial
-// sums over n/32 terms, the 32 lane partials are added in FP64.
+// Batched local solve z = X_i t_i for every block of a set in one persistent launch: the work items are
+// binned by block size (largest blocks first) and each item carries its bin's shape, L lanes per row
+// (8, 16 or 32; 256 / L rows in flight per CTA) and its row count (chosen per bin by pns_autotune).  CTAs
+// take items from a global counter until the list is exhausted.  Item = (block, first row, rows, L).
+// Output (FP64) by `mode`: 0 z[idx[row]] = y, 1 z[idx[row]] += y (atomic: overlapping dual grids),
+// 2 packed zp[row] = y, 3 packed zp[row] += y.  The dot products run in the packed type PT (FP32 for the
+// FP32/BF16 inverses): per-lane partial sums, the lane partials added in FP64.
 template <typename ST, typename PT>
-__global__ void __launch_bounds__(256) k_local_gemv(const int4* __restrict__ items, const int* __restrict__ idx,
-                                                    const long long* __restrict__ ioff, const int* __restrict__ bld,
-                                                    const long long* __restrict__ moff, const ST* __restrict__ mat,
-                                                    const PT* __restrict__ pk, double* __restrict__ z, int mode) {
-  int4 it = items[blockIdx.x];
-  int b = it.x;
-  int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int ld = bld[b];
-  const PT* x = pk + ioff[b];
-  const ST* M = mat + moff[b];
+__global__ void __launch_bounds__(256) k_local_gemv_p(const int4* __restrict__ items, int nitems,
+                                                      int* __restrict__ counter, const int* __restrict__ idx,
+                                                      const long long* __restrict__ ioff, const int* __restrict__ bld,
+                                                      const long long* __restrict__ moff, const ST* __restrict__ mat,
+                                                      const PT* __restrict__ pk, double* __restrict__ z, int mode) {
+  __shared__ int s_item;
   constexpr int W = VecW<ST>::n;
-  for (int r = it.y + warp; r < it.y + it.z; r += 8) {
-    const ST* row = M + (long long)r * ld;
-    PT acc = (PT)0;
-    for (int c = lane * W; c < ld; c += 32 * W) acc += dot16(row + c, x + c);
-    double a = (double)acc;
-    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-    if (lane == 0) {
-      const long long slot = ioff[b] + r;
-      if (mode == 0) z[idx[slot]] = a;
-      else if (mode == 1) atomicAdd(z + idx[slot], a);
-      else if (mode == 2) z[slot] = a;
-      else z[slot] += a;
+  for (;;) {
+    if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
+    __syncthreads();
+    const int i = s_item;
+    __syncthreads();
+    if (i >= nitems) return;
+    const int4 it = items[i];
+    const int L = it.w;
+    const int groups = 256 / L;
+    const int g = threadIdx.x / L, lane = threadIdx.x % L;
+    const int b = it.x;
+    const int ld = bld[b];
+    const PT* x = pk + ioff[b];
+    const ST* M = mat + moff[b];
+    const int end = it.y + it.z;
+    // the trip count is uniform within a warp (all its lane groups step together) so that the shuffles
+    // below see every lane
+    for (int base = it.y; base < end; base += groups) {
+      const int r = base + g;
+      PT acc = (PT)0;
+      if (r < end) {
+        const ST* row = M + (long long)r * ld;
+        for (int c = lane * W; c < ld; c += L * W) acc += dot16(row + c, x + c);
+      }
+      double a = (double)acc;
+      for (int o = L >> 1; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o, L);
+      if (lane == 0 && r < end) {
+        const long long slot = ioff[b] + r;
+        if (mode == 0) z[idx[slot]] = a;
+        else if (mode == 1) atomicAdd(z + idx[slot], a);
+        else if (mode == 2) z[slot] = a;
+        else z[slot] += a;
+      }
     }
   }
 }
@@ -1408,6 +1428,34 @@ template cudaError_t launch_block_mm<double, double>(const BlockSet&, const doub
 template cudaError_t launch_block_mm<float, float>(const BlockSet&, const float*, const double*, const long long*,
                                                    const int*, double*, cudaStream_t);
 
+// One persistent launch of the binned local GEMV over a block set (items and counter built by
+// build_gemv_items): a grid of a few CTAs per SM that drain the item list.
+template <typename ST, typename PT>
+cudaError_t launch_local_gemv_p(const BlockSet& B, const ST* mat, const PT* pk, double* z, int mode, cudaStream_t s) {
+  if (B.nitems_p == 0) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(B.counter.p, 0, sizeof(int), s);
+  if (e != cudaSuccess) return e;
+  static int grid = 0;
+  if (!grid) {
+    int dev = 0, sms = 148, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_local_gemv_p<float, float>, 256, 0);
+    grid = sms * std::max(1, per);
+  }
+  pns::count_launch();
+  k_local_gemv_p<ST, PT><<<(unsigned)std::min(grid, B.nitems_p), 256, 0, s>>>(
+      B.items_p.as<int4>(), B.nitems_p, B.counter.as<int>(), B.idx.as<int>(), B.d_ioff.as<long long>(),
+      B.d_ld.as<int>(), B.d_moff.as<long long>(), mat, pk, z, mode);
+  return cudaGetLastError();
+}
+template cudaError_t launch_local_gemv_p<double, double>(const BlockSet&, const double*, const double*, double*, int,
+                                                         cudaStream_t);
+template cudaError_t launch_local_gemv_p<float, float>(const BlockSet&, const float*, const float*, double*, int,
+                                                       cudaStream_t);
+template cudaError_t launch_local_gemv_p<__nv_bfloat16, float>(const BlockSet&, const __nv_bfloat16*, const float*,
+                                                               double*, int, cudaStream_t);
+
 template <typename ST, typename PT>
 cudaError_t launch_local_solve(const BlockSet& B, const ST* mat, const double* t, double* z, PT* pk_x, int add,
                                cudaStream_t s) {
@@ -1415,8 +1463,8 @@ cudaError_t launch_local_solve(const BlockSet& B, const ST* mat, const double* t
   int thr = 256;
   long long blk = (B.n_total + thr - 1) / thr;
   { pns::count_launch(); k_gather<PT><<<(unsigned)blk, thr, 0, s>>>(B.idx.as<int>(), B.n_total, t, pk_x); }
-  { pns::count_launch(); k_local_gemv<ST, PT><<<B.nitems, 256, 0, s>>>(B.items.as<int4>(), B.idx.as<int>(), B.d_ioff.as<long long>(),
-                                                B.d_ld.as<int>(), B.d_moff.as<long long>(), mat, pk_x, z, add ? 1 : 0); }
+  cudaError_t e = launch_local_gemv_p<ST, PT>(B, mat, pk_x, z, add ? 1 : 0, s);
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 
@@ -1429,15 +1477,14 @@ cudaError_t launch_local_solve_refined(const Ctx& C, const BlockSet& B, int op, 
   if (B.nblk == 0) return cudaSuccess;
   int thr = 256;
   unsigned blk = (unsigned)((B.n_total + thr - 1) / thr);
-  const int4* items = B.items.as<int4>();
   { pns::count_launch(); k_gather<PT><<<blk, thr, 0, s>>>(B.idx.as<int>(), B.n_total, t, pk_x); }
-  { pns::count_launch(); k_local_gemv<ST, PT><<<B.nitems, 256, 0, s>>>(items, B.idx.as<int>(), B.d_ioff.as<long long>(),
-                                                B.d_ld.as<int>(), B.d_moff.as<long long>(), mat, pk_x, zp, 2); }
+  cudaError_t e = launch_local_gemv_p<ST, PT>(B, mat, pk_x, zp, 2, s);
+  if (e != cudaSuccess) return e;
   { pns::count_launch(); k_local_residual<PT><<<blk, thr, 0, s>>>(C.G, C.P, C.flags.as<uint8_t>(), op, state, B.nblk,
                                                 B.d_ioff.as<long long>(), B.d_n.as<int>(), B.idx.as<int>(), B.n_total,
                                                 t, zp, pk_x); }
-  { pns::count_launch(); k_local_gemv<ST, PT><<<B.nitems, 256, 0, s>>>(items, B.idx.as<int>(), B.d_ioff.as<long long>(),
-                                                B.d_ld.as<int>(), B.d_moff.as<long long>(), mat, pk_x, zp, 3); }
+  e = launch_local_gemv_p<ST, PT>(B, mat, pk_x, zp, 3, s);
+  if (e != cudaSuccess) return e;
   { pns::count_launch(); k_scatter_packed<<<blk, thr, 0, s>>>(B.idx.as<int>(), B.n_total, zp, z, add); }
   return cudaGetLastError();
 }

@@ -23,7 +23,6 @@ long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
 
 namespace {
 
-constexpr int GEMV_ROWS = 32;   // rows per local-solve work item (8 warps x 4 rows)
 
 int fail(Ctx& C, int code, const char* what, cudaError_t e = cudaSuccess) {
   char buf[512];
@@ -80,6 +79,25 @@ int vt_bytes(int precision) { return precision == PNS_FP64 ? 8 : 4; }
 int st_bytes(int precision) { return precision == PNS_FP64 ? 8 : (precision == PNS_FP32 ? 4 : 2); }
 
 // --------------------------------------------------------------------------- block sets
+// Binned work list of the persistent local GEMV: blocks in descending size, each cut into items of its
+// bin's row count and tagged with its bin's lanes per row (tune[bin] = config id).
+int build_gemv_items(Ctx& C, BlockSet& B, const int* tune) {
+  std::vector<int> order(B.nblk);
+  for (int b = 0; b < B.nblk; ++b) order[b] = b;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return B.n[a] > B.n[b]; });
+  std::vector<int4> items;
+  for (int b : order) {
+    const int cfg = tune[tune_bin(B.n[b])];
+    const int R = TUNE_ROWS[cfg], L = TUNE_LANES[cfg];
+    for (int r = 0; r < B.n[b]; r += R) items.push_back(make_int4(b, r, std::min(R, B.n[b] - r), L));
+  }
+  B.nitems_p = (int)items.size();
+  if (B.nblk == 0) return PNS_OK;
+  CK(upload(B.items_p, items, C.stream));
+  if (!B.counter.p) CK(dalloc(B.counter, sizeof(int)));
+  return PNS_OK;
+}
+
 int make_blockset(Ctx& C, BlockSet& B, const std::vector<std::vector<int>>& lists) {
   B.nblk = (int)lists.size();
   B.n.resize(B.nblk);
@@ -105,12 +123,9 @@ int make_blockset(Ctx& C, BlockSet& B, const std::vector<std::vector<int>>& list
   B.ioff[B.nblk] = B.n_total;
   B.moff[B.nblk] = B.m_total;
   std::vector<int> idx(B.n_total, -1);
-  std::vector<int4> items;
   for (int b = 0; b < B.nblk; ++b) {
     std::copy(lists[b].begin(), lists[b].end(), idx.begin() + B.ioff[b]);
-    for (int r = 0; r < B.n[b]; r += GEMV_ROWS) items.push_back(make_int4(b, r, std::min(GEMV_ROWS, B.n[b] - r), 0));
   }
-  B.nitems = (int)items.size();
   std::vector<long long> ioff(B.ioff.begin(), B.ioff.end() - 1), moff(B.moff.begin(), B.moff.end() - 1);
   if (B.nblk == 0) return PNS_OK;
   CK(upload(B.idx, idx, C.stream));
@@ -118,8 +133,7 @@ int make_blockset(Ctx& C, BlockSet& B, const std::vector<std::vector<int>>& list
   CK(upload(B.d_ld, B.ld, C.stream));
   CK(upload(B.d_ioff, ioff, C.stream));
   CK(upload(B.d_moff, moff, C.stream));
-  CK(upload(B.items, items, C.stream));
-  return PNS_OK;
+  return build_gemv_items(C, B, C.tune);
 }
 
 int op_of_variant(int variant) {
@@ -1064,6 +1078,106 @@ int pns_precond_apply(pns_ctx* ctx, const double* v, double* z) {
   if (check_ctx(ctx) || !v || !z) return PNS_ERR_ARG;
   Ctx& C = ctx->c;
   return precond_apply(C, C.pc, v, z);
+}
+
+int pns_set_tuning(pns_ctx* ctx, const int* table) {
+  if (check_ctx(ctx) || !table) return PNS_ERR_ARG;
+  Ctx& C = ctx->c;
+  for (int b = 0; b < TUNE_BINS; ++b)
+    if (table[b] < 0 || table[b] >= TUNE_CONFIGS) return fail(C, PNS_ERR_ARG, "tuning table: config id out of range");
+  for (int b = 0; b < TUNE_BINS; ++b) C.tune[b] = table[b];
+  for (BlockSet* B : {&C.pc.prim, &C.pc.dual, &C.pc.bs.bf, &C.pc.bs.bl})
+    if (B->nblk && B->idx.p) CKS(build_gemv_items(C, *B, C.tune));
+  return PNS_OK;
+}
+
+int pns_autotune(pns_ctx* ctx, int* table, double* ms) {
+  if (check_ctx(ctx)) return PNS_ERR_ARG;
+  Ctx& C = ctx->c;
+  Precond& pc = C.pc;
+  if (!pc.built || pc.variant == PNS_BLOCK_SCHUR) return fail(C, PNS_ERR_STATE, "pns_autotune needs a built PLMM preconditioner");
+  const cudaStream_t s = C.stream;
+  const long long pkn = std::max(1LL, std::max(pc.prim.n_total, pc.dual.n_total));
+  DevBuf out, pk;
+  CK(dalloc(out, sizeof(double) * pkn));
+  CK(dalloc(pk, sizeof(double) * pkn));
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  std::vector<double> t(TUNE_BINS * TUNE_CONFIGS, 0.0);
+  int saved[TUNE_BINS];
+  for (int b = 0; b < TUNE_BINS; ++b) saved[b] = C.tune[b];
+  int rc = PNS_OK;
+  for (int bin = 0; bin < TUNE_BINS && rc == PNS_OK; ++bin) {
+    for (int cfg = 0; cfg < TUNE_CONFIGS && rc == PNS_OK; ++cfg) {
+      for (BlockSet* B : {&pc.prim, &pc.dual}) {
+        if (B->nblk == 0) continue;
+        // a work list of this bin's blocks only, in this config
+        BlockSet& S = *B;
+        std::vector<int> keep;
+        for (int q = 0; q < S.nblk; ++q)
+          if (tune_bin(S.n[q]) == bin) keep.push_back(q);
+        if (keep.empty()) continue;
+        std::vector<int4> items;
+        for (int q : keep)
+          for (int r = 0; r < S.n[q]; r += TUNE_ROWS[cfg])
+            items.push_back(make_int4(q, r, std::min(TUNE_ROWS[cfg], S.n[q] - r), TUNE_LANES[cfg]));
+        DevBuf saved_items;
+        saved_items.p = S.items_p.p;
+        saved_items.bytes = S.items_p.bytes;
+        const int saved_n = S.nitems_p;
+        S.items_p.p = nullptr;
+        S.items_p.bytes = 0;
+        cudaError_t e = upload(S.items_p, items, s);
+        S.nitems_p = (int)items.size();
+        float best = 1e30f;
+        for (int rep = 0; rep < 6 && e == cudaSuccess; ++rep) {
+          cudaEventRecord(e0, s);
+          if (pc.precision == PNS_FP64)
+            e = launch_local_gemv_p<double, double>(S, S.mat.as<double>(), pk.as<double>(), out.as<double>(), 2, s);
+          else if (pc.precision == PNS_FP32)
+            e = launch_local_gemv_p<float, float>(S, S.mat.as<float>(), pk.as<float>(), out.as<double>(), 2, s);
+          else
+            e = launch_local_gemv_p<__nv_bfloat16, float>(S, S.mat.as<__nv_bfloat16>(), pk.as<float>(),
+                                                          out.as<double>(), 2, s);
+          cudaEventRecord(e1, s);
+          if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+          float msr = 0;
+          if (e == cudaSuccess && rep > 0 && cudaEventElapsedTime(&msr, e0, e1) == cudaSuccess) best = std::min(best, msr);
+        }
+        S.items_p.release();
+        S.items_p.p = saved_items.p;
+        S.items_p.bytes = saved_items.bytes;
+        saved_items.p = nullptr;
+        S.nitems_p = saved_n;
+        if (e != cudaSuccess) {
+          rc = fail(C, PNS_ERR_CUDA, "pns_autotune", e);
+          break;
+        }
+        t[bin * TUNE_CONFIGS + cfg] += best;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) return rc;
+  int best[TUNE_BINS];
+  for (int bin = 0; bin < TUNE_BINS; ++bin) {
+    best[bin] = saved[bin];
+    double bt = 1e300;
+    for (int cfg = 0; cfg < TUNE_CONFIGS; ++cfg) {
+      const double v = t[bin * TUNE_CONFIGS + cfg];
+      if (v > 0 && v < bt) {
+        bt = v;
+        best[bin] = cfg;
+      }
+    }
+  }
+  if (table)
+    for (int b = 0; b < TUNE_BINS; ++b) table[b] = best[b];
+  if (ms)
+    for (int q = 0; q < TUNE_BINS * TUNE_CONFIGS; ++q) ms[q] = t[q];
+  return pns_set_tuning(ctx, best);
 }
 
 int pns_newton_solve(pns_ctx* ctx, double* x, const double* x_prev, pns_stats* st) {

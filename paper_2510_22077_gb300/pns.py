@@ -17,6 +17,10 @@ VARIANTS = {"gplmm": GPLMM, "aplmm_ns": APLMM_NS, "aplmm_s": APLMM_S, "ml_only":
 FP64, FP32, BF16 = 0, 1, 2
 PRECISIONS = {"fp64": FP64, "fp32": FP32, "bf16": BF16}
 COMBINE_BUILD, COMBINE_CURRENT = 0, 1
+TUNE_BINS, TUNE_CONFIGS = 6, 6
+# (lanes per row, rows per work item) of each local-solve config id, and the block-size bin edges
+TUNE_SHAPES = [(8, 32), (8, 128), (16, 32), (16, 128), (32, 16), (32, 64)]
+TUNE_BIN_EDGES = [64, 256, 1024, 4096, 16384]
 
 STATUS = {0: "PNS_OK", -1: "PNS_ERR_ARG", -2: "PNS_ERR_CUDA", -3: "PNS_ERR_OOM", -4: "PNS_ERR_SINGULAR",
           -5: "PNS_ERR_NOT_CONVERGED", -6: "PNS_ERR_NAN", -7: "PNS_ERR_STATE", -8: "PNS_ERR_TIMEOUT"}
@@ -102,6 +106,8 @@ def load(path: str = LIB_PATH):
         "pns_export_maps": (I, [P, P, P, P, P, P, P]),
         "pns_export_coarse": (I, [P, P, ctypes.POINTER(ctypes.c_int)]),
         "pns_maps_host": (I, [I, I, I, P, P, P, I, I, P, P, P, P, P, P, P]),
+        "pns_autotune": (I, [P, P, P]),
+        "pns_set_tuning": (I, [P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -259,6 +265,20 @@ class Solver:
         z = self.zeros() if z is None else z
         self._check(self.lib.pns_precond_apply_static(self.ctx, _ptr(v), _ptr(z)), "pns_precond_apply_static")
         return z
+
+    def pns_autotune(self):
+        """Time every local-solve shape on every block-size bin of the built preconditioner and adopt the
+        fastest per bin; returns (table, ms) with ms[bin][config] (0 where a bin has no block)."""
+        table = (ctypes.c_int * TUNE_BINS)()
+        ms = (ctypes.c_double * (TUNE_BINS * TUNE_CONFIGS))()
+        self._check(self.lib.pns_autotune(self.ctx, ctypes.cast(table, ctypes.c_void_p), ctypes.cast(ms, ctypes.c_void_p)),
+                    "pns_autotune")
+        return list(table), np.array(list(ms)).reshape(TUNE_BINS, TUNE_CONFIGS)
+
+    def pns_set_tuning(self, table):
+        """Adopt a local-solve tuning table (one config id per block-size bin)."""
+        t = (ctypes.c_int * TUNE_BINS)(*[int(v) for v in table])
+        self._check(self.lib.pns_set_tuning(self.ctx, ctypes.cast(t, ctypes.c_void_p)), "pns_set_tuning")
 
     def pns_newton_solve(self, x, x_prev=None, check=True):
         """Newton-FGMRES from the initial guess x, updated in place; returns the statistics as a dict

@@ -3,12 +3,17 @@
 differences): forward, parameter gradients of the masked MSE loss, one Adam step, the sample encodings,
 and a short fit.
 
-The library keeps activations and working weights in BF16 and accumulates in FP32, so it is compared with
-the oracle run in FP64 on the same (FP32 master) weights.  Bars, from the arithmetic: each of the <= 9
-stacked layers rounds its input and weights to BF16 (relative 2^-9 per factor) and its output again, so
-the network output carries a few 1e-3 of relative error and the gradients about 1e-2; the bars are 3e-2
-(output) and 6e-2 (gradients, relative L2 over each parameter tensor), where a wrong tap order, a
-transposed weight, a missing bias or a dropped skip connection leaves an O(1) error."""
+The library keeps activations, working weights and back-propagated gradients in BF16 and accumulates in
+FP32.  Two comparisons:
+* against the oracle in FP64 on the same (FP32 master) weights -- the output to 3e-2 relative L2 and
+  every gradient tensor to 0.15 (BF16 rounding of every stored tensor, compounded through up to 2L + 6
+  layers of back-propagation, with ReLU masks flipping where a pre-activation rounds across zero);
+* against the oracle's layer functions run in FP64 with the library's BF16 roundings applied at the same
+  points (inputs, weights, every stored activation and gradient) -- 3e-3 on the output and 1e-2 on each
+  gradient tensor: what remains is the FP32 accumulation order, through the elements whose BF16 rounding
+  or ReLU mask it flips (measured: up to 1.8e-3 and 4.1e-3 on the 4-level network, 20x closer than to the
+  FP64 oracle); a wrong tap order, a transposed weight, a missing bias or a dropped skip connection leaves
+  an O(1) error in either."""
 import numpy as np
 import pytest
 
@@ -55,6 +60,64 @@ def _rel(a, b):
     return float(np.linalg.norm(np.asarray(a, np.float64) - b) / max(np.linalg.norm(b), 1e-300))
 
 
+def bf16(a):
+    """Round to the nearest BF16 (ties to even), returned as float64."""
+    f = np.ascontiguousarray(a, dtype=np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    u = ((u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000).astype(np.uint32)
+    return u.view(np.float32).astype(np.float64)
+
+
+def emulated(ref, x, t, w):
+    """Forward and parameter gradients of the network with the library's BF16 roundings: inputs and weights
+    rounded, each convolution accumulated in high precision, biased, rectified and rounded; the head output
+    unrounded; the output gradient rounded; data gradients masked by (input > 0) and rounded; the upsampling
+    gradient summed and rounded; the pooling gradient added to the skip gradient and rounded."""
+    P = {k: (bf16(v) if k.endswith(".w") else v) for k, v in ref.params.items()}
+    L = ref.L
+    conv = lambda n, a: ou.conv3d(a, P[n + ".w"], ref.params[n + ".b"])
+    act = lambda n, a: bf16(np.maximum(conv(n, a), 0.0))
+    inp, e0, e1, args, shapes = [bf16(x)], [], [], [], []
+    for l in range(L):
+        e0.append(act(f"enc{l}.0", inp[l]))
+        e1.append(act(f"enc{l}.1", e0[l]))
+        if l < L - 1:
+            p_, a_ = ou.maxpool2(e1[l])
+            args.append(a_)
+            shapes.append(e1[l].shape)
+            inp.append(p_)
+    h = {L - 1: e1[L - 1]}
+    cat, d0 = {}, {}
+    for l in range(L - 2, -1, -1):
+        cat[l] = np.concatenate([ou.upsample2(h[l + 1]), e1[l]], axis=1)
+        d0[l] = act(f"dec{l}.0", cat[l])
+        h[l] = act(f"dec{l}.1", d0[l])
+    out = conv("head", h[0])
+    _, gout = ou.masked_mse(out, t, w)
+    grads = {}
+
+    def back(n, xin, g, want_dx):
+        gx, gw, gb = ou.conv3d_backward(xin, P[n + ".w"], g)
+        grads[n + ".w"], grads[n + ".b"] = gw, gb
+        return bf16(gx * (xin > 0)) if want_dx else None
+
+    g = back("head", h[0], bf16(gout), True)          # gradient of the pre-activation of h[0]
+    g_skip = {}
+    for l in range(0, L - 1):
+        g = back(f"dec{l}.1", d0[l], g, True)
+        gc = back(f"dec{l}.0", cat[l], g, True)
+        cu = h[l + 1].shape[1]
+        g_skip[l] = gc[:, cu:]
+        g = bf16(ou.upsample2_backward(gc[:, :cu]))  # gradient of the pre-activation of h[l + 1]
+    g_e1 = {L - 1: g}
+    for l in range(L - 1, -1, -1):
+        g0 = back(f"enc{l}.1", e0[l], g_e1[l], True)
+        gp = back(f"enc{l}.0", inp[l], g0, l > 0)
+        if l > 0:
+            g_e1[l - 1] = bf16(g_skip[l - 1] + ou.maxpool2_backward(args[l - 1], gp, shapes[l - 1]))
+    return out, grads
+
+
 @pytest.mark.parametrize("channels,shape,batch", [((8,), (8, 8, 8), 2), ((8, 16), (8, 8, 16), 2),
                                                   ((16, 32, 64, 64), (16, 16, 16), 1)])
 def test_forward_and_gradients_match_oracle(channels, shape, batch):
@@ -81,10 +144,18 @@ def test_forward_and_gradients_match_oracle(channels, shape, batch):
         lines.append(f"{n}: {e:.2e}")
         worst = max(worst, e)
         off += sz
-    print(f"U-Net {channels} {shape} x{batch}: output rel err {e_out:.2e}; gradient rel err worst {worst:.2e} "
-          f"({', '.join(lines)})")
-    assert e_out < 3e-2
-    assert worst < 6e-2
+    out_e, grads_e = emulated(ref, x, t, w)
+    e_out_e = _rel(out_g, out_e)
+    off = 0
+    worst_e = 0.0
+    for n in names:
+        sz = ref.params[n].size
+        worst_e = max(worst_e, _rel(gg[off:off + sz], grads_e[n].ravel()))
+        off += sz
+    print(f"U-Net {channels} {shape} x{batch}: output rel err {e_out:.2e} (FP64 oracle), {e_out_e:.2e} (BF16-rounded "
+          f"oracle); gradient rel err worst {worst:.2e} (FP64), {worst_e:.2e} (BF16-rounded) ({', '.join(lines)})")
+    assert e_out < 3e-2 and e_out_e < 3e-3
+    assert worst < 0.15 and worst_e < 1e-2
 
 
 def test_adam_step_matches_oracle():
