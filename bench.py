@@ -67,6 +67,14 @@ def parse(argv=None):
     ap.add_argument("--sample-n", type=int, default=64)
     ap.add_argument("--heldout", default="64:9000-9007,96:9000-9001",
                     help="held-out images as size:first-last seed ranges")
+    ap.add_argument("--autotune", action="store_true",
+                    help="run the local-solve autotuner on the workload's gPLMM preconditioner and print its table "
+                         "(the table the library ships, paper_2510_22077_gb300/tuning_gb300.json, came from this)")
+    ap.add_argument("--transient", action="store_true",
+                    help="the transient configuration instead of the main line: 128^3 sphere pack at porosity 0.40 "
+                         "(pores split above 5400 cells), Re 50, dt for CFL 1, backward Euler from rest with one "
+                         "aPLMM_NS build reused for every step")
+    ap.add_argument("--be-steps", type=int, default=50)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--precisions", default="fp64,fp32,bf16",
@@ -391,6 +399,9 @@ def one_solve(w, mu, variant, precision, gj=None):
     try:
         S = pns.Solver(w.mask, w.labels, 1.0, mu, (1.0, 0.0, 0.0), variant=variant, precision=precision,
                        timing=True, gj_tensor_cores=gj)
+        tt, _ = load_tuning()
+        if tt:
+            S.pns_set_tuning(tt)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
         e0.record(S.stream)
@@ -421,6 +432,96 @@ def compare_precisions(args):
     for prec in [p.strip() for p in args.precisions.split(",") if p.strip()]:
         out[prec] = one_solve(w, mu, "gplmm", prec, args.gj)
     return out
+
+
+def run_transient(args):
+    """Backward Euler through the library: the aPLMM_NS preconditioner built once at the state of rest and
+    reused by the Newton solve of every time step (Sec. 8.2); each step timed with CUDA events."""
+    import numpy as np
+    import torch
+    from paper_2510_22077_gb300 import inputs, pns
+    n = args.n if args.n != 96 else 128
+    w = inputs.make_workload("spheres", seed=args.seed, n=n, porosity=0.40, target=474, split_cells=5400)
+    re = 50.0
+    mu = inputs.mu_kozeny_carman(w.mask, re)
+    U = re * mu / inputs.characteristic_length(w.mask)
+    dt = 1.0 / U
+    S = pns.Solver(w.mask, w.labels, 1.0, mu, (1.0, 0.0, 0.0), dt, variant="aplmm_ns", precision=args.precision,
+                   timing=True, gj_tensor_cores=args.gj)
+    tt, _ = load_tuning()
+    if tt:
+        S.pns_set_tuning(tt)
+    info = S.info()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    x_prev = S.zeros()
+    torch.cuda.synchronize()
+    e0.record(S.stream)
+    S.pns_build_precond(x_prev)
+    e1.record(S.stream)
+    torch.cuda.synchronize()
+    t_build = e0.elapsed_time(e1)
+    steps = []
+    clk = ClockSampler(0)
+    for k in range(args.be_steps):
+        x = x_prev.clone()
+        e0.record(S.stream)
+        st = S.pns_newton_solve(x, x_prev, check=False)
+        e1.record(S.stream)
+        torch.cuda.synchronize()
+        steps.append({"ms": e0.elapsed_time(e1), "newton_its": st["newton_its"], "fgmres_its": st["fgmres_its"],
+                      "status": st["status"]})
+        x_prev = x
+        if st["status"] != "PNS_OK":
+            break
+    clocks = clk.stop()
+    ux = x_prev[:S.ncell].cpu().numpy().reshape(w.mask.shape)
+    its = [i for s_ in steps for i in s_["fgmres_its"]]
+    line = {"metric": "transient NS: time per backward-Euler step", "value": float(np.mean([s_["ms"] for s_ in steps])),
+            "unit": "ms", "higher_is_better": False, "n_gpus": 1, "steps": len(steps),
+            "dtype": "f64 (residual, outer Jacobian, Arnoldi) + " + args.precision + " (preconditioner)",
+            "data": "synthetic (seeded sphere pack)",
+            "config": {"workload": f"spheres{n}^3 phi=0.40 r~U[6,10] seed={args.seed}, pores split above 5400 cells, "
+                                   f"Re {re:g} (Kozeny-Carman mu), dt = h/U = {dt:.4g} (CFL 1), backward Euler from "
+                                   f"rest, aPLMM_NS built once at rest and reused", "n_unknowns": info["n_unknowns"],
+                       "n_pores": info["n_prim"], "n_interfaces": info["n_iface"], "max_block": info["max_block"],
+                       "prim_sum_n2": info["prim_sum_n2"], "dual_sum_n2": info["dual_sum_n2"], "dt": dt, "mu": mu},
+            "build_ms": t_build, "newton_its_per_step": [s_["newton_its"] for s_ in steps],
+            "fgmres_its_per_newton_step_mean": float(np.mean(its)) if its else None,
+            "fgmres_its_per_step": [s_["fgmres_its"] for s_ in steps], "ms_per_step": [s_["ms"] for s_ in steps],
+            "status_last": steps[-1]["status"] if steps else None,
+            "re_reached_last": inputs.reynolds(w.mask, ux, 1.0, mu), "clocks": clocks}
+    S.close()
+    print(json.dumps(line), flush=True)
+
+
+TUNING = os.path.join(ROOT, "paper_2510_22077_gb300", "tuning_gb300.json")
+
+
+def load_tuning():
+    """The committed local-solve tuning table (one shape id per block-size bin), or None."""
+    try:
+        d = json.load(open(TUNING))
+        return [int(v) for v in d["table"]], d
+    except (OSError, KeyError, ValueError):
+        return None, None
+
+
+def run_autotune(args):
+    """Autotune the persistent local-solve launch on this workload (gPLMM built at the Stokes iterate) and
+    print the table with the time of every (bin, shape)."""
+    from paper_2510_22077_gb300 import pns
+    w, mu = workload(args)
+    S = pns.Solver(w.mask, w.labels, 1.0, mu, (1.0, 0.0, 0.0), variant=args.variant, precision=args.precision,
+                   gj_tensor_cores=args.gj)
+    x, _ = S.pns_stokes_solve()
+    S.pns_build_precond(x)
+    table, ms = S.pns_autotune()
+    out = {"table": table, "ms": ms.tolist(), "shapes": pns.TUNE_SHAPES, "bin_edges": pns.TUNE_BIN_EDGES,
+           "workload": config(args, w, S.info())["workload"],
+           "how": "pns_autotune: best of five launches after one warm-up per (bin, shape), primary and dual sets "
+                  "summed, CUDA events, one GB300"}
+    S.close()
+    print(json.dumps(out), flush=True)
 
 
 def run_learned(args):
@@ -494,6 +595,10 @@ def main():
         return run_reference(args, rank, world)
     if args.learned:
         return run_learned(args)
+    if args.autotune:
+        return run_autotune(args)
+    if args.transient:
+        return run_transient(args)
     import torch
     dist = None
     if world > 1:
@@ -506,6 +611,9 @@ def main():
     S = pns.Solver(w.mask, w.labels, 1.0, mu, (1.0, 0.0, 0.0), variant=args.variant, precision=args.precision,
                    timing=True, gj_tensor_cores=args.gj)
     info = S.info()
+    tune_table, tune_rec = load_tuning()
+    if tune_table:
+        S.pns_set_tuning(tune_table)
     try:
         peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]
         peak_src = "measured"
@@ -599,12 +707,18 @@ def main():
                                "traffic": 1.019 * bytes_apply, "traffic_unit": "bytes per M_d + M_p pass",
                                "peak_source": peak_src, "bytes_per_apply": bytes_apply,
                                "launches_timed": launches_local, "ms_timed": t_local},
-            "roofline_jac": roof_jac, "clocks": clocks, "gpu_launches": launches}
+            "roofline_jac": roof_jac, "clocks": clocks, "gpu_launches": launches,
+            "local_solve_tuning": {"table": tune_table, "shapes": [list(v) for v in pns.TUNE_SHAPES],
+                                   "bin_edges": pns.TUNE_BIN_EDGES,
+                                   "source": "paper_2510_22077_gb300/tuning_gb300.json" if tune_table else
+                                   "library default"}}
     if rank == 0 and not args.no_e2e:
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         S2 = pns.Solver(w.mask, w.labels, 1.0, mu, (1.0, 0.0, 0.0), variant=args.variant, precision=args.precision,
                         gj_tensor_cores=args.gj)
+        if tune_table:
+            S2.pns_set_tuning(tune_table)
         x2 = S2.zeros()
         S2.pns_stokes_solve(x2)
         S2.pns_build_precond(x2)

@@ -218,7 +218,8 @@ int pns_precond_apply_static(pns_ctx* ctx, const double* v, double* z);
 /* Shapes of the batched local solves (Eq. 25: M_p and M_d applied as one persistent launch per block set).
  * The blocks are binned by size n: bin 0 n <= 64, 1 n <= 256, 2 n <= 1024, 3 n <= 4096, 4 n <= 16384,
  * 5 larger; each bin uses one of PNS_TUNE_CONFIGS shapes (lanes per matrix row, rows per work item):
- * 0 (8, 32), 1 (8, 128), 2 (16, 32), 3 (16, 128), 4 (32, 16), 5 (32, 64).  Default table {1, 3, 5, 5, 5, 5}.
+ * 0 (8, 32), 1 (8, 128), 2 (16, 32), 3 (16, 128), 4 (32, 16), 5 (32, 64).  Default table {0, 0, 2, 4, 4, 4},
+ * the choice of pns_autotune on a GB300 for the 96^3 sphere pack.
  * The paper has no counterpart: this is how this library schedules the paper's batched local solves. */
 #define PNS_TUNE_BINS 6
 #define PNS_TUNE_CONFIGS 6

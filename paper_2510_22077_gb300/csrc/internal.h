@@ -63,7 +63,7 @@ inline int tune_bin(int n) {
 }
 constexpr int TUNE_LANES[TUNE_CONFIGS] = {8, 8, 16, 16, 32, 32};
 constexpr int TUNE_ROWS[TUNE_CONFIGS] = {32, 128, 32, 128, 16, 64};
-constexpr int TUNE_DEFAULT[TUNE_BINS] = {1, 3, 5, 5, 5, 5};
+constexpr int TUNE_DEFAULT[TUNE_BINS] = {0, 0, 2, 4, 4, 4};   // pns_autotune on a GB300, 96^3 pack
 
 // Block-triangular Schur comparator (variant PNS_BLOCK_SCHUR): pore blocks of F and L = B2 D^-1 B1 for
 // block Jacobi, D = diag(F), and the workspace of its inner GMRES.

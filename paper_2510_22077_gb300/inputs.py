@@ -682,6 +682,7 @@ def make_workload(kind: str, seed: int = 0, **kw) -> Workload:
         mask = sphere_pack_3d(n, kw.get("rmin", 6.0), kw.get("rmax", 10.0), kw.get("porosity", 0.35), seed)
         target = kw.get("target", 200)
         min_cells, max_cells = 135, 5400   # ~500 and ~20k unknowns (3.7 unknowns per void cell)
+        split = kw.get("split_cells", 0)
     elif kind == "grf":
         n = kw.get("n", 256)
         mask = gaussian_field_3d(n, kw.get("corr_len", 8.0), kw.get("porosity", 0.20), seed)

@@ -39,8 +39,11 @@ def solve_pair(w, re, precision="fp32", newton_tol=1e-8):
     Returns (solver, x_stokes, x_ns, stats) or None when a solve fails."""
     import torch
     mu = inputs.mu_kozeny_carman(w.mask, re)
-    S = pns.Solver(w.mask, w.labels, 1.0, mu, (1.0, 0.0, 0.0), variant="gplmm", precision=precision,
-                   newton_tol=newton_tol)
+    try:
+        S = pns.Solver(w.mask, w.labels, 1.0, mu, (1.0, 0.0, 0.0), variant="gplmm", precision=precision,
+                       newton_tol=newton_tol, max_newton=15, max_fgmres=600)
+    except pns.PnsError:
+        return None
     try:
         xs, _ = S.pns_stokes_solve()
         x = xs.clone()
@@ -71,10 +74,14 @@ class Dataset:
         seed = seed0
         while k < n_samples and seed < seed0 + 4 * n_samples:
             kind = "spheres" if seed % 2 == 0 else "grf"
-            w, phi = _image(kind, seed, n)
             re = float(np.random.default_rng(seed + 7).uniform(re_min, re_max))
             seed += 1
-            r = solve_pair(w, re)
+            try:
+                w, phi = _image(kind, seed - 1, n)
+            except (ValueError, ZeroDivisionError):
+                w = None
+            # an image without a void path along x (possible for a small Gaussian field) has no flow
+            r = solve_pair(w, re) if w is not None and w.mask.any() else None
             if r is None:
                 self.skipped += 1
                 continue
