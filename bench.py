@@ -29,6 +29,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "time to 1e-8 Newton residual"
+# DRAM bytes measured by ncu per algorithmic byte, for the kernels of the current build (profiles/*.md); a
+# kernel missing here has no capture of its current version and reports no traffic
+TRAFFIC_RATIO = {}
 UNIT = "ms"
 
 
@@ -72,7 +75,7 @@ def parse(argv=None):
                          "(the table the library ships, paper_2510_22077_gb300/tuning_gb300.json, came from this)")
     ap.add_argument("--transient", action="store_true",
                     help="the transient configuration instead of the main line: 128^3 sphere pack at porosity 0.40 "
-                         "(pores split above 5400 cells), Re 50, dt for CFL 1, backward Euler from rest with one "
+                         "(labeller target 1400 pores), Re 50, dt for CFL 1, backward Euler from rest with one "
                          "aPLMM_NS build reused for every step")
     ap.add_argument("--be-steps", type=int, default=50)
     ap.add_argument("--no-e2e", action="store_true")
@@ -149,7 +152,7 @@ class ClockSampler:
 # The FP64 oracle timed on the host cores.  Every figure is a measured run of the oracle's own steps
 # (oracle/: maps, operator assembly, SuperLU factorisations of the local and closure blocks as
 # oracle.plmm.Plmm makes them, their solves, a Jacobian apply, one Gram-Schmidt pass).  The local blocks
-# are split into N_STRATA strata (every N_STRATA-th block in size order, primary and dual grids alike);
+# are split into N_STRATA strata (dealt in snake order over the size ranking, primary and dual grids alike);
 # a bounded sample measures some strata in full, and the build and apply times of the sample are scaled
 # by N_STRATA / (strata measured): with all strata measured (the reference arm at --steps >= N_STRATA)
 # the whole build is measured and nothing is scaled.
@@ -176,7 +179,13 @@ def _strata(pb, n_strata):
     kinds = [("p", i, len(P)) for i, P in enumerate(m.prim_unknowns)] + \
             [("d", j, len(D)) for j, D in enumerate(m.dual_unknowns)]
     kinds.sort(key=lambda t: (-t[2], t[0], t[1]))
-    return [kinds[s::n_strata] for s in range(n_strata)], np
+    # snake order over the size ranking (0..S-1, S-1..0, ...): every stratum gets blocks of every size and
+    # about the same share of the work
+    strata = [[] for _ in range(n_strata)]
+    for r, kd in enumerate(kinds):
+        q, m = divmod(r, n_strata)
+        strata[m if q % 2 == 0 else n_strata - 1 - m].append(kd)
+    return strata, np
 
 
 def _time_blocks(pb, A, blocks):
@@ -310,10 +319,12 @@ def compose_oracle(recs, summ, its, its_src):
     return total, build, it, scale
 
 
-def cpu_baseline(w, mu, its_gpu, strata=(0, 1), mt=True, stored_its=True):
+def cpu_baseline(w, mu, its_gpu, strata=(9, 10), mt=True, stored_its=True):
     """The FP64 oracle on one host core on a bounded sample of the workload: the strata given (2 of 20:
-    a tenth of the local blocks, every size represented) measured in full, scaled to all blocks; plus the
-    same sample on all host cores (process pool) as a labelled multi-threaded figure."""
+    a tenth of the local blocks, every size represented; the two middle strata of the snake order, whose
+    blocks sit mid-rank in every group of 20, so that the heavy tail of block sizes is not over-weighted)
+    measured in full, scaled to all blocks; plus the same sample on all host cores (process pool) as a
+    labelled multi-threaded figure.  The reference arm measures every stratum."""
     its, its_src = oracle_iterations() if stored_its else (None, None)
     if its is None:
         its, its_src = its_gpu, "FGMRES iterations of this run's GPU solve (no stored oracle solve)"
@@ -329,7 +340,7 @@ def cpu_baseline(w, mu, its_gpu, strata=(0, 1), mt=True, stored_its=True):
                       f"in full: maps {summ['maps_s']:.1f} s, operator assembly {summ['asm_s']:.1f} s, one Jacobian "
                       f"apply {summ['jac_s'] * 1e3:.0f} ms, one Gram-Schmidt pass over 50 vectors "
                       f"{summ['orth50_s'] * 1e3:.0f} ms, the coarse LU; local and closure factorisations and one "
-                      f"solve of each measured in full on {len(recs)} of {N_STRATA} size strata "
+                      f"solve of each measured in full on {len(recs)} of {N_STRATA} strata (snake order over the sizes) "
                       f"({sum(r['blocks'] for r in recs)} of {summ['n_blocks']} blocks, {wall:.0f} s) and scaled x"
                       f"{scale:g}: one build {build:.0f} s, one FGMRES iteration {it:.2f} s; total = maps + assembly "
                       f"+ 2 builds + {its} iterations ({its_src})"),
@@ -441,7 +452,7 @@ def run_transient(args):
     import torch
     from paper_2510_22077_gb300 import inputs, pns
     n = args.n if args.n != 96 else 128
-    w = inputs.make_workload("spheres", seed=args.seed, n=n, porosity=0.40, target=474, split_cells=5400)
+    w = inputs.make_workload("spheres", seed=args.seed, n=n, porosity=0.40, target=1400)
     re = 50.0
     mu = inputs.mu_kozeny_carman(w.mask, re)
     U = re * mu / inputs.characteristic_length(w.mask)
@@ -452,6 +463,7 @@ def run_transient(args):
     if tt:
         S.pns_set_tuning(tt)
     info = S.info()
+    print(json.dumps({"transient_setup": info}), file=sys.stderr, flush=True)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     x_prev = S.zeros()
     torch.cuda.synchronize()
@@ -470,6 +482,7 @@ def run_transient(args):
         torch.cuda.synchronize()
         steps.append({"ms": e0.elapsed_time(e1), "newton_its": st["newton_its"], "fgmres_its": st["fgmres_its"],
                       "status": st["status"]})
+        print(json.dumps({"be_step": k, **steps[-1]}), file=sys.stderr, flush=True)
         x_prev = x
         if st["status"] != "PNS_OK":
             break
@@ -480,7 +493,7 @@ def run_transient(args):
             "unit": "ms", "higher_is_better": False, "n_gpus": 1, "steps": len(steps),
             "dtype": "f64 (residual, outer Jacobian, Arnoldi) + " + args.precision + " (preconditioner)",
             "data": "synthetic (seeded sphere pack)",
-            "config": {"workload": f"spheres{n}^3 phi=0.40 r~U[6,10] seed={args.seed}, pores split above 5400 cells, "
+            "config": {"workload": f"spheres{n}^3 phi=0.40 r~U[6,10] seed={args.seed}, labeller target 1400 pores, "
                                    f"Re {re:g} (Kozeny-Carman mu), dt = h/U = {dt:.4g} (CFL 1), backward Euler from "
                                    f"rest, aPLMM_NS built once at rest and reused", "n_unknowns": info["n_unknowns"],
                        "n_pores": info["n_prim"], "n_interfaces": info["n_iface"], "max_block": info["max_block"],
@@ -534,11 +547,12 @@ def run_learned(args):
     t0 = time.time()
     n = args.sample_n
     net = pns.UNet(channels=(16, 32, 64, 64), in_ch=6, out_ch=4, batch=4, shape=(n, n, n), seed=args.seed)
-    data = learned.Dataset(net, args.samples, n=n, seed0=1000)
+    log = lambda m: print(m, file=sys.stderr, flush=True)   # noqa: E731
+    data = learned.Dataset(net, args.samples, n=n, seed0=1000, log=log)
     t_data = time.time() - t0
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(net.stream)
-    hist = learned.train(net, data, epochs=args.epochs, batch=4, lr=1e-3, seed=args.seed)
+    hist = learned.train(net, data, epochs=args.epochs, batch=4, lr=1e-3, seed=args.seed, log=log)
     e1.record(net.stream)
     torch.cuda.synchronize()
     t_train = e0.elapsed_time(e1) / 1e3
@@ -558,7 +572,8 @@ def run_learned(args):
             else:
                 net_eval = net
             try:
-                r = learned.compare_on(w, re, net_eval)
+                r = learned.compare_on(w, re, net_eval, gain=data.gain)
+                log(f"held-out {size}^3 seed {seed}: {r}")
             except Exception as ex:   # recorded
                 r = {"error": f"{type(ex).__name__}: {ex}"[:200]}
             evals.append({"size": int(size), "seed": seed, "kind": kind, "phi": phi, "re": re, **r})
@@ -665,7 +680,7 @@ def main():
     # batched local-solve kernel over the timed region: event times and launch counts are cumulative
     # per context, so take the difference to the end of the last warm-up step
     base = last[2] if last is not None else {"t_local_ms": 0.0, "local_launches": 0, "kernel_launches": 0,
-                                             "t_gj_update_ms": 0.0, "gj_update_flops": 0.0,
+                                             "t_gj_update_ms": 0.0, "gj_update_flops": 0.0, "gj_update_bytes": 0.0,
                                              "gj_update_launches": 0, "gj_update_tiles": 0}
     bytes_apply = st["local_bytes_per_apply"]
     launches_local = st["local_launches"] - base["local_launches"]
@@ -676,12 +691,33 @@ def main():
     # peak from unit counts: SMs x 128 FP32 FMA lanes x 2 flops x the maximum SM clock
     gj_ms = st["t_gj_update_ms"] - base["t_gj_update_ms"]
     gj_fl = st["gj_update_flops"] - base["gj_update_flops"]
+    gj_by = st["gj_update_bytes"] - base.get("gj_update_bytes", 0.0)
     gj_n = st["gj_update_launches"] - base["gj_update_launches"]
     gj_tiles = st["gj_update_tiles"] - base["gj_update_tiles"]
-    sms = torch.cuda.get_device_properties(local_rank).multi_processor_count
-    mhz = (clocks or {}).get("sm_max_mhz") or 2070.0
-    fp32_peak = sms * 128 * 2 * mhz * 1e6 / 1e12
+    gj_kind = {0: "fma", 1: "mma.sync", 2: "tcgen05", 3: "tcgen05-tile"}.get(args.gj if args.gj is not None else 2)
     gj_achieved = gj_fl / (gj_ms * 1e-3) / 1e12 if gj_ms > 0 else None
+    gj_gbs = gj_by / (gj_ms * 1e-3) / 1e9 if gj_ms > 0 else None
+    try:
+        pk = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        bf16_peak, bf16_src = pk["bf16_tflops"], "measured"
+    except (OSError, KeyError, ValueError):
+        bf16_peak, bf16_src = 1900.0, "fallback"
+    # TF32 dense rate = the measured BF16 rate x the nominal TF32 / BF16 ratio (1.1 / 2.25); the update runs
+    # three TF32 products per FP32 product, so its FP32-equivalent tensor ceiling is a third of that
+    tf32_peak = bf16_peak * 1.1 / 2.25
+    fp32_eq_peak = tf32_peak / 3.0
+    roof_gj = {"kernel": "k_gj_update_tcp (FP32 Gauss-Jordan trailing update of the local inverses, tcgen05 "
+                         "kind::tf32 with a 3-term split, persistent)" if gj_kind == "tcgen05" else
+                         f"Gauss-Jordan trailing update ({gj_kind})",
+               "bound": "hbm", "achieved": gj_gbs, "peak": peak, "unit": "GB/s",
+               "frac": (gj_gbs / peak) if gj_gbs else None,
+               "traffic": (TRAFFIC_RATIO["k_gj_update_tcp"] * gj_by / gj_n
+                           if TRAFFIC_RATIO.get("k_gj_update_tcp") and gj_n and gj_kind == "tcgen05" else None),
+               "peak_source": peak_src,
+               "bytes_timed": gj_by, "flops_timed": gj_fl, "launches_timed": gj_n, "ms_timed": gj_ms,
+               "tensor": {"achieved": gj_achieved, "unit": "TFLOP/s (FP32 products)", "peak": fp32_eq_peak,
+                          "frac": (gj_achieved / fp32_eq_peak) if gj_achieved else None,
+                          "peak_source": f"{bf16_src} BF16 {bf16_peak:g} TFLOP/s x 1.1/2.25 (TF32) / 3 products"}}
     roof_jac = time_jacobian(S, info, peak=peak)
     roof_jac["peak_source"] = peak_src
     S.close()
@@ -692,19 +728,19 @@ def main():
             "fgmres_its": {"stokes": its_stokes, "newton": its_newton, "per_newton_step": st["fgmres_its"]},
             "newton_its": st["newton_its"], "res_hist": st["res_hist"], "re_reached": re_reached,
             "buckets_ms": {"t_ml": st["t_ml_ms"], "t_mg": st["t_mg_ms"], "t_sol_newton": st["t_sol_ms"],
-                           "t_sol_stokes": sst["t_sol_ms"]},
-            # traffic: DRAM bytes per launch, scaled from the ncu captures of the same kernels on the 48^3
-            # pack (profiles/): update 0.979 x its C-tile bytes, local solve 1.019 x its algorithmic bytes
-            "roofline": {"kernel": "k_mm128_gj_update (FP32 Gauss-Jordan trailing update of the local inverses)",
-                         "bound": "alu", "achieved": gj_achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                         "frac": (gj_achieved / fp32_peak) if gj_achieved else None,
-                         "traffic": (0.979 * gj_tiles * 128 * 128 * 8 / gj_n) if gj_n else None,
-                         "peak_source": f"derived: {sms} SMs x 128 FP32 lanes x 2 x {mhz:g} MHz",
-                         "flops_timed": gj_fl, "launches_timed": gj_n, "ms_timed": gj_ms},
-            "roofline_apply": {"kernel": "k_local_gemv (batched local solves M_d, M_p; with its gather)",
+                           "t_sol_stokes": sst["t_sol_ms"],
+                           "t_mg_parts": dict(zip(["closure_solves", "coarse_matrix", "coarse_inverse"],
+                                                  st["t_mg_parts_ms"]))},
+            # traffic: DRAM bytes per unit, scaled from the ncu captures of the same kernels on the 48^3 pack
+            # (profiles/) by the units processed (TRAFFIC_RATIO: measured DRAM bytes / algorithmic bytes)
+            "roofline": roof_gj,
+            "roofline_apply": {"kernel": "k_local_gemv_p (persistent size-binned local solves M_d, M_p; with their "
+                                         "gather and refinement residual)",
                                "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                                "frac": (achieved / peak) if achieved else None,
-                               "traffic": 1.019 * bytes_apply, "traffic_unit": "bytes per M_d + M_p pass",
+                               "traffic": (TRAFFIC_RATIO["k_local_gemv_p"] * bytes_apply
+                                           if TRAFFIC_RATIO.get("k_local_gemv_p") else None),
+                               "traffic_unit": "bytes per M_d + M_p pass",
                                "peak_source": peak_src, "bytes_per_apply": bytes_apply,
                                "launches_timed": launches_local, "ms_timed": t_local},
             "roofline_jac": roof_jac, "clocks": clocks, "gpu_launches": launches,
@@ -774,8 +810,8 @@ def run_reference(args, rank, world):
     ms_step = 1e3 * sum(step_s) / len(step_s)
     v = total * 1e3
     cb = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-          "sample": (f"each step: one of {N_STRATA} size strata of the local blocks (every {N_STRATA}th block in size "
-                     f"order) factorised and solved in full by the oracle, 1 thread; {len(uniq)} strata measured "
+          "sample": (f"each step: one of {N_STRATA} strata of the local blocks (dealt in snake order over the size "
+                     f"ranking) factorised and solved in full by the oracle, 1 thread; {len(uniq)} strata measured "
                      f"({'all blocks, nothing scaled' if scale == 1 else f'scaled x{scale:g}'}); fixed costs measured "
                      f"once: maps {summ['maps_s']:.1f} s, assembly {summ['asm_s']:.1f} s, Jacobian apply "
                      f"{summ['jac_s'] * 1e3:.0f} ms, Gram-Schmidt pass {summ['orth50_s'] * 1e3:.0f} ms; value = maps + "

@@ -133,6 +133,10 @@ typedef struct pns_stats {
   double gj_update_flops;         /* its algorithmic flops, 2 (n - nb)^2 nb per block and step (cumulative) */
   long long gj_update_launches;   /* its timed launches (cumulative) */
   long long gj_update_tiles;      /* 128 x 128 output tiles it processed (cumulative) */
+  double t_mg_parts_ms[3];        /* t_mg of the last build split into: closure solves (shape and correction
+                                     vectors), assembly of A^o, inversion of A^o */
+  double gj_update_bytes;         /* algorithmic bytes of the timed update launches: the trailing matrix read and
+                                     written and the two panels read, FP32, per block and step (cumulative) */
 } pns_stats;
 
 typedef struct pns_info {

@@ -38,7 +38,8 @@ typedef struct pns_unet pns_unet;
 
 /* Create a network and the device buffers for inputs of shape (batch, in_ch, nz, ny, nx); later calls
  * may use any batch <= `batch` and any dimensions whose voxel count does not exceed nz*ny*nx and that
- * are multiples of 2^(levels-1).  Parameters start as He-normal weights (seeded) and zero biases.
+ * are multiples of 2^(levels-1).  Parameters start as He-normal weights (seeded), zero biases and a zero head
+ * (so that the untrained network proposes no correction).
  * channels: `levels` entries.  stream: a cudaStream_t (NULL = legacy default).  Synchronises. */
 int pns_unet_create(pns_unet** out, int levels, const int* channels, int in_ch, int out_ch, int batch, int nz,
                     int ny, int nx, uint64_t seed, void* stream);

@@ -106,7 +106,7 @@ struct Precond {
 
 // CUDA-event timing of the FP32 Gauss-Jordan update launches (cumulative; read after a synchronise)
 struct GjTimer {
-  double ms = 0, flops = 0;
+  double ms = 0, flops = 0, bytes = 0;   // bytes: the trailing matrix read and written once per step plus the panels
   long long launches = 0, tiles = 0;
 };
 
@@ -141,6 +141,7 @@ struct Ctx {
   const double* cur_state = nullptr;   // Newton state for COMBINE_CURRENT
   double t_setup_ms = 0;
   double t_mg_ms = 0, t_ml_ms = 0;
+  double t_mg_parts[3] = {0, 0, 0};  // closure solves (shape / correction vectors), A^o assembly, A^o inverse
   GjTimer gj;                    // update-kernel timing of the local-inverse builds (timing == 1)
   int tune[TUNE_BINS] = {TUNE_DEFAULT[0], TUNE_DEFAULT[1], TUNE_DEFAULT[2], TUNE_DEFAULT[3], TUNE_DEFAULT[4],
                          TUNE_DEFAULT[5]};   // config of each size bin of the persistent local GEMV

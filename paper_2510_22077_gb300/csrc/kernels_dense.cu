@@ -1285,7 +1285,7 @@ cudaError_t launch_gj_invert(const BlockSet& B, ST* mat, int* d_bad, cudaStream_
   if (B.nblk == 0) return cudaSuccess;
   constexpr int TBK = GjPanel<ST>::tb;
   std::vector<cudaEvent_t> evs;
-  double flops = 0;
+  double flops = 0, bytes = 0;
   long long tiles = 0;
   // order blocks by tile count (descending): the active set at step k is a prefix
   std::vector<int> order(B.nblk);
@@ -1352,6 +1352,7 @@ cudaError_t launch_gj_invert(const BlockSet& B, ST* mat, int* d_bad, cudaStream_
               const int n = B.n[order[q]];
               const int nb = std::min(TBK, n - k * TBK);
               flops += 2.0 * (double)(n - nb) * (double)(n - nb) * (double)nb;
+              bytes += 8.0 * (double)(n - nb) * (double)(n - nb) + 8.0 * (double)(n - nb) * (double)nb;
             }
             tiles += pre2[cnt];
           }
@@ -1387,6 +1388,7 @@ cudaError_t launch_gj_invert(const BlockSet& B, ST* mat, int* d_bad, cudaStream_
       if (cudaEventElapsedTime(&ms, evs[q], evs[q + 1]) == cudaSuccess) timer->ms += ms;
     }
     timer->flops += flops;
+    timer->bytes += bytes;
     timer->tiles += tiles;
     timer->launches += (long long)(evs.size() / 2);
   }

@@ -278,6 +278,7 @@ int build_coarse_t(Ctx& C, Precond& pc, int* d_bad) {
   CK(upload(pc.d_coloff, coloff, s));
   CK(upload(pc.d_boff, roffv, s));
   long long rtot = roff[M.n_prim];
+  const double tc0 = now_ms();
   DevBuf rhs, out;
   CK(dalloc(rhs, sizeof(double) * std::max(1LL, rtot)));
   CK(dalloc(out, sizeof(double) * std::max(1LL, rtot)));
@@ -311,6 +312,8 @@ int build_coarse_t(Ctx& C, Precond& pc, int* d_bad) {
   // and the coarse solve then amplifies the rounding along that mode.
   CK(dalloc(pc.basis, sizeof(double) * std::max(1LL, rtot)));
   CK(cudaMemcpyAsync(pc.basis.p, out.p, sizeof(double) * rtot, cudaMemcpyDeviceToDevice, s));
+  CK(cudaStreamSynchronize(s));
+  const double tc1 = now_ms();
   // coarse matrix A^o = R^ A_b P^ column by column (prolong e_k, apply A_b, restrict)
   const int no = pc.n_o;
   // A primary grid on which b_B = rho b vanishes (no face unknown along a nonzero component of b) has
@@ -347,6 +350,8 @@ int build_coarse_t(Ctx& C, Precond& pc, int* d_bad) {
   for (int i = 0; i < M.n_prim; ++i)
     if (no_source[i]) { pns::count_launch(); k_unitrow<<<(no + 255) / 256, 256, 0, s>>>(Ao.as<double>(), no, pc.n_cif + i); }
   CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(s));
+  const double tc2 = now_ms();
   CK(dalloc(work, sizeof(double) * no));
   CK(dalloc(perm, sizeof(int) * no));
   CK(launch_coarse_invert(Ao.as<double>(), no, work.as<double>(), perm.as<int>(), d_bad, s));
@@ -358,6 +363,9 @@ int build_coarse_t(Ctx& C, Precond& pc, int* d_bad) {
   Ao.p = nullptr;
   Ao.bytes = 0;
   CK(cudaStreamSynchronize(s));
+  C.t_mg_parts[0] = tc1 - tc0;
+  C.t_mg_parts[1] = tc2 - tc1;
+  C.t_mg_parts[2] = now_ms() - tc2;
   return PNS_OK;
 }
 
@@ -868,6 +876,7 @@ int newton(Ctx& C, Precond& pc, int stokes, double* x, const double* x_prev, pns
   loc.t_sol_ms = tsol;
   loc.t_setup_ms = C.t_setup_ms;
   loc.t_mg_ms = C.t_mg_ms;
+  for (int q = 0; q < 3; ++q) loc.t_mg_parts_ms[q] = C.t_mg_parts[q];
   loc.t_ml_ms = C.t_ml_ms;
   loc.t_local_ms = C.t_local_ms;
   loc.local_launches = C.local_launches;
@@ -876,6 +885,7 @@ int newton(Ctx& C, Precond& pc, int stokes, double* x, const double* x_prev, pns
   loc.refine_residual_max = pc.ns_residual_before;
   loc.t_gj_update_ms = C.gj.ms;
   loc.gj_update_flops = C.gj.flops;
+  loc.gj_update_bytes = C.gj.bytes;
   loc.gj_update_launches = C.gj.launches;
   loc.gj_update_tiles = C.gj.tiles;
   if (stt) *stt = loc;

@@ -1037,10 +1037,11 @@ int pns_unet_create(pns_unet** out, int levels, const int* channels, int in_ch, 
       rc = PNS_ERR_OOM;
       break;
     }
-    // He-normal weights, zero biases
+    // He-normal weights, zero biases, a zero head (the untrained network proposes no correction)
     std::vector<float> p(off, 0.f);
     std::mt19937_64 gen(seed);
-    for (const ConvL& c : U->convs) {
+    for (size_t q = 0; q + 1 < U->convs.size(); ++q) {
+      const ConvL& c = U->convs[q];
       std::normal_distribution<float> nd(0.f, std::sqrt(2.0f / (float)(c.cin * c.taps)));
       for (long long i = 0; i < (long long)c.cout * c.cin * c.taps; ++i) p[c.woff + i] = nd(gen);
     }

@@ -10,7 +10,9 @@ this module only sequences the calls.
   solution by gPLMM Newton-FGMRES.  Inputs are the encoded (mask, Stokes, log10 Re) channels, targets the
   scaled NS - Stokes difference, the loss weight the void mask.  Images whose solve fails (an iteration
   cap, a singular closure block of the labelling) are skipped and counted.
-* Training: minibatches of `batch` samples, masked MSE, Adam.
+* Training: minibatches of `batch` samples, masked MSE, Adam.  The network learns the targets scaled by
+  one gain per channel (the reciprocal of the channel's RMS over the void cells of the training set), so
+  that every channel is O(1); the proposal divides the gains out again.
 * Guarded start: the network proposes x_p = Stokes + decoded correction; Newton starts from x_p only if
   ||r(x_p)|| < ||r(x_Stokes)|| (the Newton residual judges the proposal), else from the Stokes solution.
 """
@@ -96,6 +98,15 @@ class Dataset:
                 log(f"sample {k}/{n_samples} ({kind}, Re {re:.1f}, newton {st['newton_its']}) "
                     f"{time.time() - t0:.0f} s")
         self.m = k
+        # per-channel gains: the targets are trained at unit RMS over the void cells
+        self.gain = torch.ones(4, dtype=torch.float32, device="cuda")
+        if k:
+            wsum = self.w[:k].sum()
+            for c in range(4):
+                rms = torch.sqrt((self.w[:k, 0] * self.t[:k, c] ** 2).sum() / wsum)
+                if float(rms) > 0:
+                    self.gain[c] = 1.0 / rms
+            self.t[:k] *= self.gain.view(1, 4, 1, 1, 1)
         self.seconds = time.time() - t0
 
 
@@ -117,15 +128,18 @@ def train(net: pns.UNet, data: Dataset, epochs=20, batch=4, lr=1e-3, seed=0, log
     return hist
 
 
-def guarded_start(S: pns.Solver, net: pns.UNet, mask, re, xs):
+def guarded_start(S: pns.Solver, net: pns.UNet, mask, re, xs, gain=None):
     """The initial Newton iterate: the network's proposal if its Newton residual is below the Stokes
-    solution's, else the Stokes solution.  Returns (x0, used_network, ||r(x_p)|| / ||r(x_s)||)."""
+    solution's, else the Stokes solution.  `gain` (4 channels) is the target scaling the network was trained
+    with.  Returns (x0, used_network, ||r(x_p)|| / ||r(x_s)||)."""
     import torch
     nz, ny, nx = mask.shape
     f = torch.zeros((1, 6, nz, ny, nx), dtype=torch.float32, device="cuda")
     m = torch.as_tensor(mask.astype(np.uint8)).cuda()
     sc = net.features(m, xs, re, f)
     out = net.forward(f)
+    if gain is not None:
+        out = (out / gain.view(1, 4, 1, 1, 1)).contiguous()
     xp = torch.zeros_like(xs)
     net.proposal(out, xs, sc, xp)
     rp = float(S.pns_residual(xp).norm())
@@ -135,7 +149,7 @@ def guarded_start(S: pns.Solver, net: pns.UNet, mask, re, xs):
     return xs.clone(), False, rp / rs
 
 
-def compare_on(w, re, net: pns.UNet, precision="fp32"):
+def compare_on(w, re, net: pns.UNet, precision="fp32", gain=None):
     """Newton from the Stokes solution and from the guarded learned start on one image: Newton iterations,
     FGMRES iterations and the time of each (CUDA events on the solver's stream; the Stokes solve and the
     network inference are counted in the learned path's time, the Stokes solve in both)."""
@@ -150,7 +164,7 @@ def compare_on(w, re, net: pns.UNet, precision="fp32"):
         xs, _ = S.pns_stokes_solve()
         ratio, used = None, False
         if mode == "learned":
-            x, used, ratio = guarded_start(S, net, w.mask, re, xs)
+            x, used, ratio = guarded_start(S, net, w.mask, re, xs, gain)
         else:
             x = xs.clone()
         S.pns_build_precond(x)

@@ -49,7 +49,8 @@ class Stats(ctypes.Structure):
                 ("local_launches", ctypes.c_longlong), ("local_bytes_per_apply", ctypes.c_double),
                 ("kernel_launches", ctypes.c_longlong), ("refine_residual_max", ctypes.c_double),
                 ("t_gj_update_ms", ctypes.c_double), ("gj_update_flops", ctypes.c_double),
-                ("gj_update_launches", ctypes.c_longlong), ("gj_update_tiles", ctypes.c_longlong)]
+                ("gj_update_launches", ctypes.c_longlong), ("gj_update_tiles", ctypes.c_longlong),
+                ("t_mg_parts_ms", ctypes.c_double * 3), ("gj_update_bytes", ctypes.c_double)]
 
     def as_dict(self):
         n = self.newton_its
@@ -60,7 +61,8 @@ class Stats(ctypes.Structure):
                 "local_launches": self.local_launches, "local_bytes_per_apply": self.local_bytes_per_apply,
                 "kernel_launches": self.kernel_launches, "refine_residual_max": self.refine_residual_max,
                 "t_gj_update_ms": self.t_gj_update_ms, "gj_update_flops": self.gj_update_flops,
-                "gj_update_launches": self.gj_update_launches, "gj_update_tiles": self.gj_update_tiles}
+                "gj_update_launches": self.gj_update_launches, "gj_update_tiles": self.gj_update_tiles,
+                "t_mg_parts_ms": list(self.t_mg_parts_ms), "gj_update_bytes": self.gj_update_bytes}
 
 
 class Info(ctypes.Structure):

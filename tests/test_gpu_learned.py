@@ -27,7 +27,7 @@ def test_learned_start_end_to_end():
         kind = "spheres" if seed % 2 == 0 else "grf"
         w, _ = learned._image(kind, seed, n)
         re = float(np.random.default_rng(seed + 7).uniform(1.0, 100.0))
-        r = learned.compare_on(w, re, net)
+        r = learned.compare_on(w, re, net, gain=data.gain)
         print(f"image seed {seed} ({kind}, Re {re:.1f}): stokes start newton {r['stokes']['newton_its']} fgmres "
               f"{r['stokes']['fgmres_its']} {r['stokes']['ms']:.0f} ms; learned start (used: "
               f"{r['learned']['used_network']}, residual ratio {r['learned']['residual_ratio']:.3f}) newton "
