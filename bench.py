@@ -68,6 +68,8 @@ def parse(argv=None):
     ap.add_argument("--samples", type=int, default=256)
     ap.add_argument("--epochs", type=int, default=30)
     ap.add_argument("--sample-n", type=int, default=64)
+    ap.add_argument("--kinds", default="spheres", help="image kinds of the learned-guess samples (spheres,grf)")
+    ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--heldout", default="64:9000-9007,96:9000-9001",
                     help="held-out images as size:first-last seed ranges")
     ap.add_argument("--autotune", action="store_true",
@@ -548,11 +550,12 @@ def run_learned(args):
     n = args.sample_n
     net = pns.UNet(channels=(16, 32, 64, 64), in_ch=6, out_ch=4, batch=4, shape=(n, n, n), seed=args.seed)
     log = lambda m: print(m, file=sys.stderr, flush=True)   # noqa: E731
-    data = learned.Dataset(net, args.samples, n=n, seed0=1000, log=log)
+    kinds = tuple(args.kinds.split(","))
+    data = learned.Dataset(net, args.samples, n=n, seed0=1000, log=log, kinds=kinds)
     t_data = time.time() - t0
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(net.stream)
-    hist = learned.train(net, data, epochs=args.epochs, batch=4, lr=1e-3, seed=args.seed, log=log)
+    hist = learned.train(net, data, epochs=args.epochs, batch=4, lr=args.lr, seed=args.seed, log=log)
     e1.record(net.stream)
     torch.cuda.synchronize()
     t_train = e0.elapsed_time(e1) / 1e3
@@ -561,7 +564,7 @@ def run_learned(args):
         size, rng_ = spec.split(":")
         lo, hi = (int(v) for v in rng_.split("-"))
         for seed in range(lo, hi + 1):
-            kind = "spheres" if seed % 2 == 0 else "grf"
+            kind = kinds[seed % len(kinds)]
             w, phi = learned._image(kind, seed, int(size))
             re = float(np.random.default_rng(seed + 7).uniform(1.0, 100.0))
             if int(size) != n:
@@ -583,9 +586,9 @@ def run_learned(args):
     line = {"metric": "learned Newton initial guess: Newton iterations and time to 1e-8, Stokes start vs learned start",
             "unit": "ms", "data": "synthetic (seeded sphere packs and Gaussian fields)",
             "config": {"workload": f"3D U-Net (16/32/64/64, BF16, FP32 master, Adam) trained on {data.m} solver-generated "
-                                   f"{n}^3 samples ({data.skipped} images skipped: failed solves), {args.epochs} epochs; "
-                                   f"held-out {args.heldout}", "samples": data.m, "skipped": data.skipped,
-                       "re_range": [1, 100]},
+                                   f"{n}^3 samples ({'/'.join(kinds)}; {data.skipped} images skipped: failed solves), "
+                                   f"{args.epochs} epochs; held-out {args.heldout}", "samples": data.m,
+                       "skipped": data.skipped, "re_range": [1, 100], "kinds": list(kinds)},
             "seconds": {"samples": t_data, "train": t_train}, "loss_per_epoch": hist,
             "heldout": evals,
             "summary": {"images": len(ok),

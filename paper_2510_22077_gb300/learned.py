@@ -5,7 +5,8 @@ Every numerical step runs in libpns (the solver of include/pns.h and the network
 this module only sequences the calls.
 
 * Samples: seeded synthetic images (sphere packs with porosity U[0.30, 0.45] and thresholded Gaussian
-  fields with porosity U[0.20, 0.40], alternating), Re drawn uniformly in [re_min, re_max], mu from the
+  fields with porosity U[0.20, 0.40], alternating, or sphere packs only), Re drawn uniformly in
+  [re_min, re_max], mu from the
   Kozeny-Carman estimate; the Stokes solution (the method's own initial iterate) and the Navier-Stokes
   solution by gPLMM Newton-FGMRES.  Inputs are the encoded (mask, Stokes, log10 Re) channels, targets the
   scaled NS - Stokes difference, the loss weight the void mask.  Images whose solve fails (an iteration
@@ -63,7 +64,8 @@ def solve_pair(w, re, precision="fp32", newton_tol=1e-8):
 class Dataset:
     """Encoded samples held on the device: x (M, 6, n, n, n), t (M, 4, ...), w (M, 1, ...), FP32."""
 
-    def __init__(self, net: pns.UNet, n_samples, n=64, seed0=1000, re_min=1.0, re_max=100.0, log=None):
+    def __init__(self, net: pns.UNet, n_samples, n=64, seed0=1000, re_min=1.0, re_max=100.0, log=None,
+                 kinds=("spheres", "grf")):
         import torch
         self.n = n
         self.x = torch.zeros((n_samples, 6, n, n, n), dtype=torch.float32, device="cuda")
@@ -75,7 +77,7 @@ class Dataset:
         k = 0
         seed = seed0
         while k < n_samples and seed < seed0 + 4 * n_samples:
-            kind = "spheres" if seed % 2 == 0 else "grf"
+            kind = kinds[seed % len(kinds)]
             re = float(np.random.default_rng(seed + 7).uniform(re_min, re_max))
             seed += 1
             try:

@@ -1,5 +1,5 @@
 """The learned Newton initial guess end to end on the GPU, at a small scale: solver-generated samples
-(32^3 sphere packs and Gaussian fields, Re in [1, 100]), training of the U-Net with the library's kernels,
+(32^3 sphere packs, Re in [1, 100]), training of the U-Net with the library's kernels,
 and Newton from the guarded learned start against Newton from the Stokes solution on the same image.
 
 Checks: the training loss falls; the guarded start never has a larger Newton residual than the Stokes
@@ -17,9 +17,9 @@ def test_learned_start_end_to_end():
     from paper_2510_22077_gb300 import learned, pns
     n = 32
     net = pns.UNet(channels=(16, 32, 64, 64), in_ch=6, out_ch=4, batch=4, shape=(n, n, n), seed=0)
-    data = learned.Dataset(net, 8, n=n, seed0=1000)
+    data = learned.Dataset(net, 8, n=n, seed0=1000, kinds=("spheres",))
     assert data.m == 8
-    hist = learned.train(net, data, epochs=40, batch=4, lr=2e-3)
+    hist = learned.train(net, data, epochs=150, batch=4, lr=2e-3)
     print(f"samples {data.m} (skipped {data.skipped}) in {data.seconds:.1f} s; loss {hist[0]:.3e} -> {hist[-1]:.3e}")
     assert hist[-1] < 0.5 * hist[0]
     # guarded start on a training image and on a held-out image
