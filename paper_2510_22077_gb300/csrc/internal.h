@@ -208,7 +208,7 @@ cudaError_t launch_closure_rhs(const Ctx& C, const BlockSet& B, int op, const do
                                const int* d_cols, const long long* d_roff, const int* d_kc, double* rhs);
 template <typename ST, typename AT>
 cudaError_t launch_block_mm(const BlockSet& B, const ST* mat, const double* rhs, const long long* d_roff,
-                            const int* d_kc, double* out, cudaStream_t s);
+                            const int* d_kc, const std::vector<int>& kc, double* out, cudaStream_t s);
 template <typename ST, typename PT>
 cudaError_t launch_local_solve_refined(const Ctx& C, const BlockSet& B, int op, const double* state, const ST* mat,
                                        const double* t, double* z, PT* pk_x, double* zp, int add, cudaStream_t s);

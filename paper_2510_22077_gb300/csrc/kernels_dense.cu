@@ -708,35 +708,57 @@ __global__ void k_closure_rhs(Geo G, Phy P, const uint8_t* __restrict__ fl, int 
 }
 
 // ------------------------------------------------------------------------------ X * RHS
-// out[b] (n x kc, FP64) = X_b (n x n) * rhs[b] (n x kc); one warp per row, 16 RHS columns at a time
+// Tiled X_b * R_b: one CTA per (block, 64 rows of X, 64 columns of R).  The K loop stages 64 columns of the
+// X rows and the matching 64 rows of R in shared memory, so that X is read once per 64 columns of R and R
+// once per 64 rows of X; 256 threads, a 4 x 4 register tile each.  item = (block, row tile, column tile).
 template <typename ST, typename AT>
-__global__ void k_block_mm(int nblk, const long long* __restrict__ ioff, const int* __restrict__ bn,
-                           const int* __restrict__ bld, const long long* __restrict__ moff, const ST* __restrict__ mat,
-                           long long n_total, const double* __restrict__ rhs, const long long* __restrict__ roff,
-                           const int* __restrict__ kcv, double* __restrict__ out) {
-  long long t = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
-  int lane = threadIdx.x & 31;
-  if (t >= n_total) return;
-  int b = find_block(ioff, nblk, t);
-  int r = (int)(t - ioff[b]);
-  int n = bn[b];
-  if (r >= n) return;
-  int kc = kcv[b];
-  const ST* X = mat + moff[b] + (long long)r * bld[b];
+__global__ void __launch_bounds__(256) k_block_mm_t(const int4* __restrict__ items, const int* __restrict__ bn,
+                                                    const int* __restrict__ bld, const long long* __restrict__ moff,
+                                                    const ST* __restrict__ mat, const double* __restrict__ rhs,
+                                                    const long long* __restrict__ roff, const int* __restrict__ kcv,
+                                                    double* __restrict__ out) {
+  __shared__ AT xs[64][65];
+  __shared__ AT rs[64][65];
+  const int4 it = items[blockIdx.x];
+  const int b = it.x, r0 = it.y * 64, q0 = it.z * 64;
+  const int n = bn[b], ld = bld[b], kc = kcv[b];
+  const ST* X = mat + moff[b];
   const double* R = rhs + roff[b];
-  for (int k0 = 0; k0 < kc; k0 += 16) {
-    int kn = min(16, kc - k0);
-    AT acc[16];
-    for (int q = 0; q < 16; ++q) acc[q] = (AT)0;
-    for (int cidx = lane; cidx < n; cidx += 32) {
-      AT xv = (AT)to_f(X[cidx]);
-      const double* rr = R + (long long)cidx * kc + k0;
-      for (int q = 0; q < kn; ++q) acc[q] += xv * (AT)rr[q];
+  const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
+  AT acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = (AT)0;
+  for (int c0 = 0; c0 < n; c0 += 64) {
+    __syncthreads();
+    for (int e = threadIdx.x; e < 64 * 64; e += 256) {
+      const int i = e >> 6, j = e & 63;
+      xs[i][j] = (r0 + i < n && c0 + j < n) ? (AT)to_f(X[(long long)(r0 + i) * ld + c0 + j]) : (AT)0;
+      rs[i][j] = (c0 + i < n && q0 + j < kc) ? (AT)R[(long long)(c0 + i) * kc + q0 + j] : (AT)0;
     }
-    for (int q = 0; q < kn; ++q) {
-      AT v = acc[q];
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-      if (lane == 0) out[roff[b] + (long long)r * kc + k0 + q] = (double)v;
+    __syncthreads();
+#pragma unroll 8
+    for (int k = 0; k < 64; ++k) {
+      AT a[4], bb[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = xs[ty * 4 + i][k];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) bb[j] = rs[k][tx * 4 + j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * bb[j];
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int r = r0 + ty * 4 + i;
+    if (r >= n) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int q = q0 + tx * 4 + j;
+      if (q < kc) out[roff[b] + (long long)r * kc + q] = (double)acc[i][j];
     }
   }
 }
@@ -1262,6 +1284,28 @@ __global__ void k_woodbury_update(int nblk, const long long* __restrict__ ioff, 
 }  // namespace
 
 // ================================================================================ launchers
+// Temporary device buffers of one host-side step; every allocation is checked, and everything is freed
+// when the object goes out of scope.
+struct TmpDev {
+  std::vector<void*> ptrs;
+  TmpDev() = default;
+  TmpDev(const TmpDev&) = delete;
+  TmpDev& operator=(const TmpDev&) = delete;
+  ~TmpDev() {
+    for (void* p : ptrs) cudaFree(p);
+  }
+  template <typename T>
+  cudaError_t get(T** out, size_t bytes) {
+    *out = nullptr;
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, std::max<size_t>(bytes, 1));
+    if (e != cudaSuccess) return e;
+    ptrs.push_back(p);
+    *out = (T*)p;
+    return cudaSuccess;
+  }
+};
+
 template <typename ST>
 cudaError_t launch_assemble(const Ctx& C, const BlockSet& B, int op, const double* state, ST* mat, int closure) {
   if (B.nblk == 0) return cudaSuccess;
@@ -1416,19 +1460,29 @@ cudaError_t launch_closure_rhs(const Ctx& C, const BlockSet& B, int op, const do
 
 template <typename ST, typename AT>
 cudaError_t launch_block_mm(const BlockSet& B, const ST* mat, const double* rhs, const long long* d_roff,
-                            const int* d_kc, double* out, cudaStream_t s) {
+                            const int* d_kc, const std::vector<int>& kc, double* out, cudaStream_t s) {
   if (B.nblk == 0) return cudaSuccess;
-  long long warps = B.n_total;
-  long long blk = (warps * 32 + 255) / 256;
-  { pns::count_launch(); k_block_mm<ST, AT><<<(unsigned)blk, 256, 0, s>>>(B.nblk, B.d_ioff.as<long long>(), B.d_n.as<int>(),
-                                                   B.d_ld.as<int>(), B.d_moff.as<long long>(), mat, B.n_total, rhs,
-                                                   d_roff, d_kc, out); }
-  return cudaGetLastError();
+  std::vector<int4> items;
+  for (int b = 0; b < B.nblk; ++b)
+    for (int rt = 0; rt * 64 < B.n[b]; ++rt)
+      for (int qt = 0; qt * 64 < kc[b]; ++qt) items.push_back(make_int4(b, rt, qt, 0));
+  if (items.empty()) return cudaSuccess;
+  TmpDev tmp;
+  int4* d_items = nullptr;
+  cudaError_t e = tmp.get(&d_items, sizeof(int4) * items.size());
+  if (e != cudaSuccess) return e;
+  if ((e = cudaMemcpyAsync(d_items, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice, s)) != cudaSuccess)
+    return e;
+  pns::count_launch();
+  k_block_mm_t<ST, AT><<<(unsigned)items.size(), 256, 0, s>>>(d_items, B.d_n.as<int>(), B.d_ld.as<int>(),
+                                                             B.d_moff.as<long long>(), mat, rhs, d_roff, d_kc, out);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  return cudaStreamSynchronize(s);   // the item list is freed on return
 }
 template cudaError_t launch_block_mm<double, double>(const BlockSet&, const double*, const double*, const long long*,
-                                                     const int*, double*, cudaStream_t);
+                                                     const int*, const std::vector<int>&, double*, cudaStream_t);
 template cudaError_t launch_block_mm<float, float>(const BlockSet&, const float*, const double*, const long long*,
-                                                   const int*, double*, cudaStream_t);
+                                                   const int*, const std::vector<int>&, double*, cudaStream_t);
 
 // One persistent launch of the binned local GEMV over a block set (items and counter built by
 // build_gemv_items): a grid of a few CTAs per SM that drain the item list.
@@ -1502,28 +1556,6 @@ template cudaError_t launch_local_solve<float, float>(const BlockSet&, const flo
                                                       int, cudaStream_t);
 template cudaError_t launch_local_solve<__nv_bfloat16, float>(const BlockSet&, const __nv_bfloat16*, const double*,
                                                               double*, float*, int, cudaStream_t);
-
-// Temporary device buffers of one host-side step; every allocation is checked, and everything is freed
-// when the object goes out of scope.
-struct TmpDev {
-  std::vector<void*> ptrs;
-  TmpDev() = default;
-  TmpDev(const TmpDev&) = delete;
-  TmpDev& operator=(const TmpDev&) = delete;
-  ~TmpDev() {
-    for (void* p : ptrs) cudaFree(p);
-  }
-  template <typename T>
-  cudaError_t get(T** out, size_t bytes) {
-    *out = nullptr;
-    void* p = nullptr;
-    cudaError_t e = cudaMalloc(&p, std::max<size_t>(bytes, 1));
-    if (e != cudaSuccess) return e;
-    ptrs.push_back(p);
-    *out = (T*)p;
-    return cudaSuccess;
-  }
-};
 
 // Refine the inverses of a block set: blocks whose max |I - A X| exceeds `thresh` get `steps`
 // Newton-Schulz steps.  Scratch is bounded by `budget_bytes` (blocks processed in chunks).
@@ -1825,7 +1857,7 @@ cudaError_t Woodbury::apply(const Ctx& C, const BlockSet& B, const ST* X, const 
                             const long long* d_roff, const int* d_kc, const std::vector<int>& kc) {
   cudaStream_t s = C.stream;
   WoodburyImpl& W = *impl;
-  cudaError_t e = launch_block_mm<ST, ST>(B, X, R, d_roff, d_kc, Y, s);
+  cudaError_t e = launch_block_mm<ST, ST>(B, X, R, d_roff, d_kc, kc, Y, s);
   if (e != cudaSuccess) return e;
   long long wtot = W.woff[B.nblk];
   double *Wm = nullptr, *Z = nullptr;
