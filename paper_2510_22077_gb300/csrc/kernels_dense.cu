@@ -21,8 +21,6 @@ namespace {
 
 constexpr int TB = 64;   // Gauss-Jordan panel width == tile edge
 
-__device__ __forceinline__ float to_f(float v) { return v; }
-__device__ __forceinline__ double to_f(double v) { return v; }
 
 __device__ __forceinline__ int find_block(const long long* __restrict__ off, int nb, long long t) {
   int lo = 0, hi = nb - 1;
@@ -95,17 +93,23 @@ __global__ void k_assemble(Geo G, Phy P, const uint8_t* __restrict__ fl, int op,
 // [k*TBK, k*TBK + nb).  Active blocks are the first `cnt` of `order`.  256 threads per CTA; the panel
 // kernels give each thread an R x R patch (R = TBK / 16).
 // In-place inverse of the nb x nb diagonal block of step k, one CTA per active block.  Thread
-// (ty, tx) of a 16 x 16 grid keeps the R x R patch (rows ty*R.., cols tx*R..) in registers; per pivot
-// the owners of the pivot row and column publish them in shared memory (two barriers per pivot).
-// Rows and columns past nb are zero and stay zero.
+// (ty, tx) of a 16 x 16 grid keeps the R x R patch (rows ty*R.., cols tx*R..) in registers.  Pivot t with
+// p = D[t][t], written as one rank-1 update of every entry:
+//   D[i][j] <- keep(i, j) D[i][j] - c[i] * r[j] / p,   keep = (i != t && j != t),
+//   c[i] = D[i][t] (i != t), c[t] = -1;   r[j] = D[t][j] (j != t), r[t] = 1,
+// which gives D[t][j] / p on the pivot row, -D[i][t] / p on the pivot column and 1 / p at the pivot (the
+// Gauss-Jordan step, same roundings as the row-by-row form).  The owners of row and column t + 1 publish
+// c, r and p into the other of two shared buffers right after their own update of step t, so one barrier
+// per pivot suffices; the pivot's position inside a patch is a compile-time index (the steps are unrolled
+// R at a time).  Rows and columns past nb are zero and stay zero.
 template <typename ST, int TBK>
 __global__ void __launch_bounds__(256) k_gj_diag(int k, const int* __restrict__ order, const int* __restrict__ bn,
                                                  const int* __restrict__ bld, const long long* __restrict__ moff,
                                                  ST* __restrict__ mat, int* __restrict__ bad) {
   constexpr int R = TBK / 16;
-  __shared__ ST rrow[TBK];
-  __shared__ ST colt[TBK];
-  __shared__ ST s_piv;
+  __shared__ ST rbuf[2][TBK];
+  __shared__ ST cbuf[2][TBK];
+  __shared__ ST pbuf[2];
   const int b = order[blockIdx.x];
   const int n = bn[b], ld = bld[b];
   const int p0 = k * TBK;
@@ -121,60 +125,56 @@ __global__ void __launch_bounds__(256) k_gj_diag(int k, const int* __restrict__ 
       const int i = i0 + r, j = j0 + c;
       P[r][c] = (i < nb && j < nb) ? A[(long long)i * ld + j] : (ST)0;
     }
-  for (int t = 0; t < nb; ++t) {
-    const int owner = t / R, rt = t % R;
-    if (ty == owner && tx == owner) {
-#pragma unroll
-      for (int r = 0; r < R; ++r)
-#pragma unroll
-        for (int c = 0; c < R; ++c)
-          if (r == rt && c == rt) s_piv = P[r][c];
-    }
-    __syncthreads();
-    ST piv = s_piv;
-    const bool okp = (piv == piv) && piv != (ST)0 && (double)fabs((double)piv) < 1e300;
-    if (!okp) {
-      if (threadIdx.x == 0) atomicOr(bad, 1);
-      piv = (ST)1;
-    }
-    const ST inv = (ST)1 / piv;
-    if (ty == owner) {
+  // publish pivot t = o * R + rt into buffer q: its row (with 1 at the pivot), its column (with -1 at the
+  // pivot) and its value, then clear the row and the column in the patches (the update refills them).
+  // Called only with rt a compile-time constant (after unrolling), so P is indexed statically.
+  auto publish = [&](int o, int rt, int q) {
+    const ST pv = P[rt][rt];   // meaningful in the diagonal patch only
+    if (ty == o) {
 #pragma unroll
       for (int c = 0; c < R; ++c) {
-        ST v = (ST)0;
-#pragma unroll
-        for (int r = 0; r < R; ++r)
-          if (r == rt) v = P[r][c];
-        const int j = j0 + c;
-        rrow[j] = (j == t) ? inv : v * inv;
+        rbuf[q][j0 + c] = (tx == o && c == rt) ? (ST)1 : P[rt][c];
+        P[rt][c] = (ST)0;
       }
     }
-    if (tx == owner) {
+    if (tx == o) {
 #pragma unroll
       for (int r = 0; r < R; ++r) {
-        ST v = (ST)0;
-#pragma unroll
-        for (int c = 0; c < R; ++c)
-          if (c == rt) v = P[r][c];
-        const int i = i0 + r;
-        colt[i] = (i == t) ? (ST)0 : v;
+        cbuf[q][i0 + r] = (ty == o && r == rt) ? (ST)-1 : P[r][rt];
+        P[r][rt] = (ST)0;
       }
     }
-    __syncthreads();
-    ST cr[R], rw[R];
+    if (ty == o && tx == o) pbuf[q] = pv;
+  };
+  int q = 0;
+  if (nb > 0) publish(0, 0, 0);
+  __syncthreads();
+  for (int t0 = 0; t0 < nb; t0 += R) {
+    const int o = t0 / R;
 #pragma unroll
-    for (int r = 0; r < R; ++r) cr[r] = colt[i0 + r];
+    for (int rt = 0; rt < R; ++rt) {
+      if (t0 + rt < nb) {
+        ST piv = pbuf[q];
+        const bool okp = (piv == piv) && piv != (ST)0 && (double)fabs((double)piv) < 1e300;
+        if (!okp) {
+          if (threadIdx.x == 0) atomicOr(bad, 1);
+          piv = (ST)1;
+        }
+        const ST inv = (ST)1 / piv;
+        ST cr[R], rw[R];
 #pragma unroll
-    for (int c = 0; c < R; ++c) rw[c] = rrow[j0 + c];
+        for (int r = 0; r < R; ++r) cr[r] = cbuf[q][i0 + r];
 #pragma unroll
-    for (int r = 0; r < R; ++r)
+        for (int c = 0; c < R; ++c) rw[c] = rbuf[q][j0 + c] * inv;
 #pragma unroll
-      for (int c = 0; c < R; ++c) {
-        const int i = i0 + r, j = j0 + c;
-        if (i == t) P[r][c] = rw[c];
-        else if (j == t) P[r][c] = -cr[r] * inv;
-        else P[r][c] -= cr[r] * rw[c];
+        for (int r = 0; r < R; ++r)
+#pragma unroll
+          for (int c = 0; c < R; ++c) P[r][c] -= cr[r] * rw[c];
+        if (t0 + rt + 1 < nb) publish(rt + 1 < R ? o : o + 1, (rt + 1) % R, q ^ 1);
+        __syncthreads();
+        q ^= 1;
       }
+    }
   }
 #pragma unroll
   for (int r = 0; r < R; ++r)
@@ -708,57 +708,74 @@ __global__ void k_closure_rhs(Geo G, Phy P, const uint8_t* __restrict__ fl, int 
 }
 
 // ------------------------------------------------------------------------------ X * RHS
-// Tiled X_b * R_b: one CTA per (block, 64 rows of X, 64 columns of R).  The K loop stages 64 columns of the
-// X rows and the matching 64 rows of R in shared memory, so that X is read once per 64 columns of R and R
-// once per 64 rows of X; 256 threads, a 4 x 4 register tile each.  item = (block, row tile, column tile).
-template <typename ST, typename AT>
-__global__ void __launch_bounds__(256) k_block_mm_t(const int4* __restrict__ items, const int* __restrict__ bn,
+// Y_b = X_b R_b for every block of a set (X_b: n x n FP32 / FP64 rows at leading dimension ld; R_b, Y_b:
+// n x kc FP64 rows at offset roff[b]): the products of the closure solves.  kc = |C_i| + 1 is small (2 to
+// ~30), so this is a skinny product whose cost is the one stream of X.  A CTA takes 8 RW rows of one block
+// and KQ columns of R (item = (block, first row, first column of R)): warp w keeps rows RW w.. of Y in
+// registers, and per 128-column chunk of X each lane loads 4 consecutive columns of each of its rows
+// (16 bytes) and multiplies them with the matching 4 rows of the chunk of R, which the CTA stages in
+// shared memory transposed (Rs[q][c], one 16-byte read per lane and column q).  Lane partials are summed
+// by butterfly shuffles at the end.  Accumulation in the storage precision of X.
+template <typename ST, int KQ, int RW>
+__global__ void __launch_bounds__(256) k_block_mm_s(const int4* __restrict__ items, const int* __restrict__ bn,
                                                     const int* __restrict__ bld, const long long* __restrict__ moff,
                                                     const ST* __restrict__ mat, const double* __restrict__ rhs,
                                                     const long long* __restrict__ roff, const int* __restrict__ kcv,
                                                     double* __restrict__ out) {
-  __shared__ AT xs[64][65];
-  __shared__ AT rs[64][65];
+  constexpr int CK = 128, CKP = CK + 4;
+  __shared__ __align__(16) ST Rs[KQ][CKP];
   const int4 it = items[blockIdx.x];
-  const int b = it.x, r0 = it.y * 64, q0 = it.z * 64;
+  const int b = it.x, r0 = it.y, q0 = it.z;
   const int n = bn[b], ld = bld[b], kc = kcv[b];
+  const int qn = min(KQ, kc - q0);
   const ST* X = mat + moff[b];
   const double* R = rhs + roff[b];
-  const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
-  AT acc[4][4];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int rw0 = r0 + warp * RW;
+  ST acc[RW][KQ];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < RW; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = (AT)0;
-  for (int c0 = 0; c0 < n; c0 += 64) {
+    for (int q = 0; q < KQ; ++q) acc[i][q] = (ST)0;
+  for (int c0 = 0; c0 < n; c0 += CK) {
     __syncthreads();
-    for (int e = threadIdx.x; e < 64 * 64; e += 256) {
-      const int i = e >> 6, j = e & 63;
-      xs[i][j] = (r0 + i < n && c0 + j < n) ? (AT)to_f(X[(long long)(r0 + i) * ld + c0 + j]) : (AT)0;
-      rs[i][j] = (c0 + i < n && q0 + j < kc) ? (AT)R[(long long)(c0 + i) * kc + q0 + j] : (AT)0;
+    // stage R[c0 .. c0 + 127][q0 .. q0 + KQ) transposed; consecutive threads walk q first (coalesced reads)
+    for (int e = threadIdx.x; e < KQ * CK; e += blockDim.x) {
+      const int q = e % KQ, c = e / KQ;
+      Rs[q][c] = (q < qn && c0 + c < n) ? (ST)R[(long long)(c0 + c) * kc + q0 + q] : (ST)0;
     }
     __syncthreads();
-#pragma unroll 8
-    for (int k = 0; k < 64; ++k) {
-      AT a[4], bb[4];
+    const int c = c0 + 4 * lane;
+    ST xv[RW][4];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = xs[ty * 4 + i][k];
+    for (int i = 0; i < RW; ++i) {
+      const int row = rw0 + i;
 #pragma unroll
-      for (int j = 0; j < 4; ++j) bb[j] = rs[k][tx * 4 + j];
+      for (int u = 0; u < 4; ++u) xv[i][u] = (ST)0;
+      if (row < n && c < n) {
+        // c is a multiple of 4 below n <= ld (a multiple of 8): the 4 columns lie inside the row
+        const ST* xr = X + (long long)row * ld + c;
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+        for (int u = 0; u < 4; ++u) xv[i][u] = (c + u < n) ? xr[u] : (ST)0;
+      }
+    }
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * bb[j];
+    for (int q = 0; q < KQ; ++q) {
+      const ST* rq = &Rs[q][4 * lane];
+      const ST r_0 = rq[0], r_1 = rq[1], r_2 = rq[2], r_3 = rq[3];
+#pragma unroll
+      for (int i = 0; i < RW; ++i) acc[i][q] += xv[i][0] * r_0 + xv[i][1] * r_1 + xv[i][2] * r_2 + xv[i][3] * r_3;
     }
   }
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int r = r0 + ty * 4 + i;
-    if (r >= n) continue;
+  for (int i = 0; i < RW; ++i) {
+    const int row = rw0 + i;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int q = q0 + tx * 4 + j;
-      if (q < kc) out[roff[b] + (long long)r * kc + q] = (double)acc[i][j];
+    for (int q = 0; q < KQ; ++q) {
+      ST v = acc[i][q];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0 && row < n && q < qn) out[roff[b] + (long long)row * kc + q0 + q] = (double)v;
     }
   }
 }
@@ -1093,111 +1110,24 @@ __global__ void k_closure_extras(Geo G, Phy P, const uint8_t* __restrict__ fl, i
   extra[t] = e;
 }
 
-// Cap_b[i][j] = X_b[K_i][K_j] + (i == j) / delta_i   (FP64, row-major k x k)
+// Cap_b[i][j] = X_b[K_i][K_j] + (i == j) / delta_i, the Woodbury capacitance matrix of block b (k x k, row
+// stride cld[b], in the storage precision of X); one thread per entry over the prefix epre of k^2
 template <typename ST>
-__global__ void k_cap_assemble(const int* __restrict__ order_blk, const long long* __restrict__ epre, int nb,
-                               const int* __restrict__ kv, const long long* __restrict__ koff,
-                               const long long* __restrict__ cmoff, const int* __restrict__ Klist,
+__global__ void k_cap_assemble(const long long* __restrict__ epre, int nb, const int* __restrict__ kv,
+                               const long long* __restrict__ koff, const long long* __restrict__ cmoff,
+                               const int* __restrict__ cld, const int* __restrict__ Klist,
                                const double* __restrict__ delta, const int* __restrict__ bld,
-                               const long long* __restrict__ moff, const ST* __restrict__ X, double* __restrict__ cap) {
+                               const long long* __restrict__ moff, const ST* __restrict__ X, ST* __restrict__ cap) {
   long long w = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (w >= epre[nb]) return;
-  int s = find_block(epre, nb, w);
-  int b = order_blk[s];
-  long long loc = w - epre[s];
+  int b = find_block(epre, nb, w);
+  long long loc = w - epre[b];
   int k = kv[b];
   int i = (int)(loc / k), j = (int)(loc % k);
   const int* K = Klist + koff[b];
   double v = (double)X[moff[b] + (long long)K[i] * bld[b] + K[j]];
   if (i == j) v += 1.0 / delta[koff[b] + i];
-  cap[cmoff[b] + loc] = v;
-}
-
-// batched Gauss-Jordan with partial pivoting on the active blocks (order[0 .. cnt) all have k > t)
-__global__ void k_bpiv(int t, const int* __restrict__ order, const int* __restrict__ kv,
-                       const long long* __restrict__ cmoff, const long long* __restrict__ koff, double* __restrict__ cap,
-                       double* __restrict__ colw, int* __restrict__ perm, int* __restrict__ bad) {
-  __shared__ double bv[256];
-  __shared__ int bi[256];
-  int b = order[blockIdx.x];
-  int k = kv[b];
-  double* A = cap + cmoff[b];
-  double best = -1.0;
-  int arg = t;
-  for (int i = t + threadIdx.x; i < k; i += blockDim.x) {
-    double v = fabs(A[(long long)i * k + t]);
-    if (v > best) { best = v; arg = i; }
-  }
-  bv[threadIdx.x] = best;
-  bi[threadIdx.x] = arg;
-  __syncthreads();
-  for (int sft = blockDim.x / 2; sft > 0; sft >>= 1) {
-    if (threadIdx.x < sft) {
-      if (bv[threadIdx.x + sft] > bv[threadIdx.x] ||
-          (bv[threadIdx.x + sft] == bv[threadIdx.x] && bi[threadIdx.x + sft] < bi[threadIdx.x])) {
-        bv[threadIdx.x] = bv[threadIdx.x + sft];
-        bi[threadIdx.x] = bi[threadIdx.x + sft];
-      }
-    }
-    __syncthreads();
-  }
-  int p = bi[0];
-  double pv = A[(long long)p * k + t];
-  if (!(bv[0] > 0.0) || !(bv[0] < 1e300)) {
-    if (threadIdx.x == 0) atomicOr(bad, 1);
-    pv = 1.0;
-  }
-  if (threadIdx.x == 0) perm[koff[b] + t] = p;
-  __syncthreads();   // every thread has read the pivot value before any thread swaps rows t and p
-  if (p != t)
-    for (int j = threadIdx.x; j < k; j += blockDim.x) {
-      double a = A[(long long)t * k + j];
-      A[(long long)t * k + j] = A[(long long)p * k + j];
-      A[(long long)p * k + j] = a;
-    }
-  __syncthreads();
-  double* col = colw + koff[b];
-  for (int i = threadIdx.x; i < k; i += blockDim.x) col[i] = A[(long long)i * k + t];
-  __syncthreads();
-  double inv = 1.0 / pv;
-  for (int j = threadIdx.x; j < k; j += blockDim.x) A[(long long)t * k + j] = (j == t) ? inv : A[(long long)t * k + j] * inv;
-}
-
-__global__ void k_belim(int t, const int* __restrict__ order, const long long* __restrict__ epre, int cnt,
-                        const int* __restrict__ kv, const long long* __restrict__ cmoff,
-                        const long long* __restrict__ koff, double* __restrict__ cap, const double* __restrict__ colw) {
-  long long w = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (w >= epre[cnt]) return;
-  int s = find_block(epre, cnt, w);
-  int b = order[s];
-  long long loc = w - epre[s];
-  int k = kv[b];
-  int i = (int)(loc / k), j = (int)(loc % k);
-  if (i == t) return;
-  double* A = cap + cmoff[b];
-  double f = colw[koff[b] + i];
-  if (j == t) A[loc] = -f * A[(long long)t * k + t];
-  else A[loc] -= f * A[(long long)t * k + j];
-}
-
-__global__ void k_bunperm(int nb, const long long* __restrict__ rpre, const int* __restrict__ kv,
-                          const long long* __restrict__ cmoff, const long long* __restrict__ koff,
-                          double* __restrict__ cap, const int* __restrict__ perm) {
-  long long w = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (w >= rpre[nb]) return;
-  int b = find_block(rpre, nb, w);
-  int i = (int)(w - rpre[b]);
-  int k = kv[b];
-  double* row = cap + cmoff[b] + (long long)i * k;
-  const int* pr = perm + koff[b];
-  for (int t = k - 1; t >= 0; --t) {
-    int p = pr[t];
-    if (p != t) {
-      double a = row[t];
-      row[t] = row[p];
-      row[p] = a;
-    }
-  }
+  cap[cmoff[b] + (long long)i * cld[b] + j] = (ST)v;
 }
 
 // W[b] (k x kc) = Y[b][K, :]
@@ -1214,9 +1144,10 @@ __global__ void k_gather_rows(int nb, const long long* __restrict__ rpre, const 
   for (int q = 0; q < kc; ++q) W[woff[b] + (long long)m * kc + q] = Y[roff[b] + (long long)r * kc + q];
 }
 
-// Z[b] (k x kc) = Cinv[b] (k x k) * W[b]   (warp per row)
+// Z[b] (k x kc) = Cinv[b] (k x k) * W[b]   (warp per row; FP64 accumulation)
+template <typename ST>
 __global__ void k_cap_mm(int nb, const long long* __restrict__ rpre, const int* __restrict__ kv,
-                         const long long* __restrict__ cmoff, const double* __restrict__ Cinv,
+                         const long long* __restrict__ cmoff, const int* __restrict__ cld, const ST* __restrict__ Cinv,
                          const long long* __restrict__ woff, const int* __restrict__ kcv, const double* __restrict__ W,
                          double* __restrict__ Z) {
   long long w = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
@@ -1225,13 +1156,13 @@ __global__ void k_cap_mm(int nb, const long long* __restrict__ rpre, const int* 
   int b = find_block(rpre, nb, w);
   int m = (int)(w - rpre[b]);
   int k = kv[b], kc = kcv[b];
-  const double* C = Cinv + cmoff[b] + (long long)m * k;
+  const ST* C = Cinv + cmoff[b] + (long long)m * cld[b];
   for (int q0 = 0; q0 < kc; q0 += 16) {
     int qn = min(16, kc - q0);
     double acc[16];
     for (int q = 0; q < 16; ++q) acc[q] = 0.0;
     for (int j = lane; j < k; j += 32) {
-      double c = C[j];
+      double c = (double)C[j];
       const double* wr = W + woff[b] + (long long)j * kc + q0;
       for (int q = 0; q < qn; ++q) acc[q] += c * wr[q];
     }
@@ -1461,23 +1392,39 @@ cudaError_t launch_closure_rhs(const Ctx& C, const BlockSet& B, int op, const do
 template <typename ST, typename AT>
 cudaError_t launch_block_mm(const BlockSet& B, const ST* mat, const double* rhs, const long long* d_roff,
                             const int* d_kc, const std::vector<int>& kc, double* out, cudaStream_t s) {
+  static_assert(std::is_same<ST, AT>::value, "the closure product accumulates in the storage precision");
   if (B.nblk == 0) return cudaSuccess;
-  std::vector<int4> items;
-  for (int b = 0; b < B.nblk; ++b)
-    for (int rt = 0; rt * 64 < B.n[b]; ++rt)
-      for (int qt = 0; qt * 64 < kc[b]; ++qt) items.push_back(make_int4(b, rt, qt, 0));
-  if (items.empty()) return cudaSuccess;
+  // three column widths of R: kc <= 8 (64 rows per CTA), <= 16 (32 rows), else chunks of 32 (16 rows)
+  std::vector<int4> items[3];
+  const int kq[3] = {8, 16, 32}, rows[3] = {64, 32, 16};
+  for (int b = 0; b < B.nblk; ++b) {
+    const int bin = kc[b] <= 8 ? 0 : kc[b] <= 16 ? 1 : 2;
+    for (int q0 = 0; q0 < kc[b]; q0 += kq[bin])
+      for (int r0 = 0; r0 < B.n[b]; r0 += rows[bin]) items[bin].push_back(make_int4(b, r0, q0, 0));
+  }
   TmpDev tmp;
-  int4* d_items = nullptr;
-  cudaError_t e = tmp.get(&d_items, sizeof(int4) * items.size());
-  if (e != cudaSuccess) return e;
-  if ((e = cudaMemcpyAsync(d_items, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice, s)) != cudaSuccess)
-    return e;
-  pns::count_launch();
-  k_block_mm_t<ST, AT><<<(unsigned)items.size(), 256, 0, s>>>(d_items, B.d_n.as<int>(), B.d_ld.as<int>(),
-                                                             B.d_moff.as<long long>(), mat, rhs, d_roff, d_kc, out);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  return cudaStreamSynchronize(s);   // the item list is freed on return
+  cudaError_t e = cudaSuccess;
+  for (int bin = 0; bin < 3; ++bin) {
+    if (items[bin].empty()) continue;
+    int4* d_items = nullptr;
+    if ((e = tmp.get(&d_items, sizeof(int4) * items[bin].size())) != cudaSuccess) return e;
+    if ((e = cudaMemcpyAsync(d_items, items[bin].data(), sizeof(int4) * items[bin].size(), cudaMemcpyHostToDevice,
+                             s)) != cudaSuccess)
+      return e;
+    const unsigned grid = (unsigned)items[bin].size();
+    pns::count_launch();
+    if (bin == 0)
+      k_block_mm_s<ST, 8, 8><<<grid, 256, 0, s>>>(d_items, B.d_n.as<int>(), B.d_ld.as<int>(), B.d_moff.as<long long>(),
+                                                  mat, rhs, d_roff, d_kc, out);
+    else if (bin == 1)
+      k_block_mm_s<ST, 16, 4><<<grid, 256, 0, s>>>(d_items, B.d_n.as<int>(), B.d_ld.as<int>(),
+                                                   B.d_moff.as<long long>(), mat, rhs, d_roff, d_kc, out);
+    else
+      k_block_mm_s<ST, 32, 2><<<grid, 256, 0, s>>>(d_items, B.d_n.as<int>(), B.d_ld.as<int>(),
+                                                   B.d_moff.as<long long>(), mat, rhs, d_roff, d_kc, out);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  return cudaStreamSynchronize(s);   // the item lists are freed on return
 }
 template cudaError_t launch_block_mm<double, double>(const BlockSet&, const double*, const double*, const long long*,
                                                      const int*, const std::vector<int>&, double*, cudaStream_t);
@@ -1736,11 +1683,16 @@ cudaError_t launch_add_vec(double* a, const double* b, long long n, cudaStream_t
 
 
 // ---------------------------------------------------------------------------- Woodbury driver
+// Woodbury data of one closure build: per primary block b the rows K_b whose diagonal the closure
+// modifies (k_b of them, with their extra delta), and the inverses of the capacitance matrices, kept as a
+// block set of the blocks with k_b > 0 so that the Gauss-Jordan inverse of the local blocks inverts them
+// (cmoff / cld: each original block's offset and row stride in that set's storage, 0 when k_b = 0).
 struct WoodburyImpl {
   int nblk = 0;
   std::vector<int> k;
-  DevBuf d_k, d_koff, d_cmoff, d_Klist, d_delta, d_rpre, d_woff, cap;
+  DevBuf d_k, d_koff, d_cmoff, d_cld, d_Klist, d_delta, d_rpre, d_woff;
   std::vector<long long> koff, cmoff, rpre, woff;
+  BlockSet cb;
 };
 
 Woodbury::Woodbury() : impl(new WoodburyImpl) {}
@@ -1785,67 +1737,73 @@ cudaError_t Woodbury::setup(const Ctx& C, const BlockSet& B, int op, const doubl
   W.cmoff.assign(B.nblk + 1, 0);
   W.rpre.assign(B.nblk + 1, 0);
   W.woff.assign(B.nblk + 1, 0);
-  std::vector<int> Kl;
+  std::vector<int> Kl, cld(B.nblk, 0);
   std::vector<double> dl;
+  std::vector<long long> epre(B.nblk + 1, 0);
+  BlockSet& cb = W.cb;   // a Woodbury object is set up once
   for (int b = 0; b < B.nblk; ++b) {
     for (int r = 0; r < B.n[b]; ++r) {
       double v = ex[B.ioff[b] + r];
       if (v != 0.0) { Kl.push_back(r); dl.push_back(v); }
     }
-    W.k[b] = (int)(Kl.size() - W.koff[b]);
+    const int kb = (int)(Kl.size() - W.koff[b]);
+    W.k[b] = kb;
     W.koff[b + 1] = (long long)Kl.size();
-    W.cmoff[b + 1] = W.cmoff[b] + (long long)W.k[b] * W.k[b];
-    W.rpre[b + 1] = W.rpre[b] + W.k[b];
-    W.woff[b + 1] = W.woff[b] + (long long)W.k[b] * kc[b];
+    W.rpre[b + 1] = W.rpre[b] + kb;
+    W.woff[b + 1] = W.woff[b] + (long long)kb * kc[b];
+    epre[b + 1] = epre[b] + (long long)kb * kb;
+    W.cmoff[b] = cb.m_total;
+    if (kb > 0) {
+      const int ld = (kb + 7) / 8 * 8;
+      cld[b] = ld;
+      cb.n.push_back(kb);
+      cb.ld.push_back(ld);
+      cb.ioff.push_back(cb.n_total);
+      cb.moff.push_back(cb.m_total);
+      cb.n_total += ld;
+      cb.m_total += (long long)ld * ld;
+      cb.sum_n2 += (double)kb * kb;
+      cb.nmax = std::max(cb.nmax, kb);
+    }
   }
+  W.cmoff[B.nblk] = cb.m_total;
+  cb.nblk = (int)cb.n.size();
+  cb.ioff.push_back(cb.n_total);
+  cb.moff.push_back(cb.m_total);
   if ((e = upload_i(W.d_k, W.k, s)) != cudaSuccess) return e;
   if ((e = upload_ll(W.d_koff, W.koff, s)) != cudaSuccess) return e;
   if ((e = upload_ll(W.d_cmoff, W.cmoff, s)) != cudaSuccess) return e;
+  if ((e = upload_i(W.d_cld, cld, s)) != cudaSuccess) return e;
   if ((e = upload_i(W.d_Klist, Kl, s)) != cudaSuccess) return e;
   W.d_delta.release();
   if ((e = cudaMalloc(&W.d_delta.p, sizeof(double) * std::max<size_t>(1, dl.size()))) != cudaSuccess) return e;
   W.d_delta.bytes = sizeof(double) * std::max<size_t>(1, dl.size());
-  cudaMemcpyAsync(W.d_delta.p, dl.data(), sizeof(double) * dl.size(), cudaMemcpyHostToDevice, s);
+  if ((e = cudaMemcpyAsync(W.d_delta.p, dl.data(), sizeof(double) * dl.size(), cudaMemcpyHostToDevice, s)) !=
+      cudaSuccess)
+    return e;
   if ((e = upload_ll(W.d_rpre, W.rpre, s)) != cudaSuccess) return e;
   if ((e = upload_ll(W.d_woff, W.woff, s)) != cudaSuccess) return e;
-  long long ctot = W.cmoff[B.nblk];
-  W.cap.release();
-  if ((e = cudaMalloc(&W.cap.p, sizeof(double) * std::max(1LL, ctot))) != cudaSuccess) return e;
-  W.cap.bytes = sizeof(double) * std::max(1LL, ctot);
-  if (ctot == 0) return cudaStreamSynchronize(s);
-  // blocks sorted by k (descending): the active set at step t is a prefix
-  std::vector<int> order(B.nblk);
-  for (int b = 0; b < B.nblk; ++b) order[b] = b;
-  std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return W.k[a] > W.k[c]; });
-  std::vector<long long> epre(B.nblk + 1, 0);
-  for (int q = 0; q < B.nblk; ++q) epre[q + 1] = epre[q] + (long long)W.k[order[q]] * W.k[order[q]];
-  DevBuf d_order, d_epre, colw, perm;
-  if ((e = upload_i(d_order, order, s)) != cudaSuccess) return e;
+  if (cb.nblk == 0) return cudaStreamSynchronize(s);
+  if ((e = upload_i(cb.d_n, cb.n, s)) != cudaSuccess) return e;
+  if ((e = upload_i(cb.d_ld, cb.ld, s)) != cudaSuccess) return e;
+  if ((e = upload_ll(cb.d_ioff, std::vector<long long>(cb.ioff.begin(), cb.ioff.end() - 1), s)) != cudaSuccess)
+    return e;
+  if ((e = upload_ll(cb.d_moff, std::vector<long long>(cb.moff.begin(), cb.moff.end() - 1), s)) != cudaSuccess)
+    return e;
+  if ((e = cudaMalloc(&cb.mat.p, sizeof(ST) * (size_t)cb.m_total)) != cudaSuccess) return e;
+  cb.mat.bytes = sizeof(ST) * (size_t)cb.m_total;
+  if ((e = cudaMemsetAsync(cb.mat.p, 0, cb.mat.bytes, s)) != cudaSuccess) return e;
+  DevBuf d_epre;
   if ((e = upload_ll(d_epre, epre, s)) != cudaSuccess) return e;
-  if ((e = cudaMalloc(&colw.p, sizeof(double) * std::max(1LL, W.koff[B.nblk]))) != cudaSuccess) return e;
-  colw.bytes = 1;
-  if ((e = cudaMalloc(&perm.p, sizeof(int) * std::max(1LL, W.koff[B.nblk]))) != cudaSuccess) return e;
-  perm.bytes = 1;
-  cudaMemsetAsync(colw.p, 0, sizeof(double) * std::max(1LL, W.koff[B.nblk]), s);
-  cudaMemsetAsync(perm.p, 0, sizeof(int) * std::max(1LL, W.koff[B.nblk]), s);
   { pns::count_launch(); k_cap_assemble<ST><<<(unsigned)((epre[B.nblk] + 255) / 256), 256, 0, s>>>(
-      d_order.as<int>(), d_epre.as<long long>(), B.nblk, W.d_k.as<int>(), W.d_koff.as<long long>(),
-      W.d_cmoff.as<long long>(), W.d_Klist.as<int>(), W.d_delta.as<double>(), B.d_ld.as<int>(),
-      B.d_moff.as<long long>(), X, W.cap.as<double>()); }
-  int kmax = W.k[order[0]];
-  int cnt = B.nblk;
-  for (int t = 0; t < kmax; ++t) {
-    while (cnt > 0 && W.k[order[cnt - 1]] <= t) --cnt;
-    { pns::count_launch(); k_bpiv<<<cnt, 256, 0, s>>>(t, d_order.as<int>(), W.d_k.as<int>(), W.d_cmoff.as<long long>(),
-                                                      W.d_koff.as<long long>(), W.cap.as<double>(), colw.as<double>(),
-                                                      perm.as<int>(), d_bad); }
-    { pns::count_launch(); k_belim<<<(unsigned)((epre[cnt] + 255) / 256), 256, 0, s>>>(
-        t, d_order.as<int>(), d_epre.as<long long>(), cnt, W.d_k.as<int>(), W.d_cmoff.as<long long>(),
-        W.d_koff.as<long long>(), W.cap.as<double>(), colw.as<double>()); }
-  }
-  { pns::count_launch(); k_bunperm<<<(unsigned)((W.rpre[B.nblk] + 127) / 128), 128, 0, s>>>(
-      B.nblk, W.d_rpre.as<long long>(), W.d_k.as<int>(), W.d_cmoff.as<long long>(), W.d_koff.as<long long>(),
-      W.cap.as<double>(), perm.as<int>()); }
+      d_epre.as<long long>(), B.nblk, W.d_k.as<int>(), W.d_koff.as<long long>(), W.d_cmoff.as<long long>(),
+      W.d_cld.as<int>(), W.d_Klist.as<int>(), W.d_delta.as<double>(), B.d_ld.as<int>(), B.d_moff.as<long long>(), X,
+      cb.mat.as<ST>()); }
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  // the capacitance inverses, by the same blocked Gauss-Jordan (no pivoting) as the local inverses: on the
+  // tensor cores in the FP32 build; a zero or non-finite pivot raises the build's singular flag
+  if ((e = launch_gj_invert<ST>(cb, cb.mat.as<ST>(), d_bad, s, nullptr, C.opt.gj_tensor_cores)) != cudaSuccess)
+    return e;
   e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
@@ -1869,8 +1827,9 @@ cudaError_t Woodbury::apply(const Ctx& C, const BlockSet& B, const ST* X, const 
     { pns::count_launch(); k_gather_rows<<<(unsigned)((W.rpre[B.nblk] + 127) / 128), 128, 0, s>>>(
         B.nblk, W.d_rpre.as<long long>(), W.d_k.as<int>(), W.d_koff.as<long long>(), W.d_Klist.as<int>(), d_roff,
         W.d_woff.as<long long>(), d_kc, Y, Wm); }
-    { pns::count_launch(); k_cap_mm<<<(unsigned)((W.rpre[B.nblk] * 32 + 255) / 256), 256, 0, s>>>(
-        B.nblk, W.d_rpre.as<long long>(), W.d_k.as<int>(), W.d_cmoff.as<long long>(), W.cap.as<double>(),
+    { pns::count_launch(); k_cap_mm<ST><<<(unsigned)((W.rpre[B.nblk] * 32 + 255) / 256), 256, 0, s>>>(
+        B.nblk, W.d_rpre.as<long long>(), W.d_k.as<int>(), W.d_cmoff.as<long long>(), W.d_cld.as<int>(),
+        W.cb.mat.as<ST>(),
         W.d_woff.as<long long>(), d_kc, Wm, Z); }
   }
   { pns::count_launch(); k_woodbury_update<ST><<<(unsigned)((B.n_total * 32 + 255) / 256), 256, 0, s>>>(

@@ -251,23 +251,31 @@ __global__ void __launch_bounds__(128, 1) k_gj_update_tc(int k, int cnt, const i
 }
 
 // --------------------------------------------------------------------------------- persistent update
-// The same update as k_gj_update_tc, persistent and warp-specialised so that the load, the tensor-core
-// product and the write-back of consecutive tiles overlap: one CTA per SM walks the tiles
-// blockIdx.x, blockIdx.x + gridDim.x, ...; warp 0 (one thread) streams the operand chunks through the two
-// stages and, once the previous tile's write-back has read the C buffer, the next C tile; warp 1 (one
-// thread) issues the MMAs of each tile into one of two 128-column TMEM accumulators; warps 2-5 read an
-// accumulator back (warp w owns TMEM lanes 32 (w % 4) ..), update the C tile in shared memory and store
-// it with TMA.  A wait that times out raises the CTA's abort flag, which ends every role's loop.
+// The same update as k_gj_update_tc, persistent and warp-specialised so that the C traffic of consecutive
+// tiles never stops: one CTA per SM walks the tiles blockIdx.x, blockIdx.x + gridDim.x, ...
+//  * warp 0 (one thread) streams the operand chunks of each tile through NST stages;
+//  * warp 6 (one thread) streams the C boxes (128 rows x 32 columns, four per tile) through a ring of NCS
+//    slots, so that the loads of the next tile's C run while the current tile is written back;
+//  * warp 1 (one thread) issues the MMAs of each tile into one of two 128-column TMEM accumulators;
+//  * warps 2-5 read an accumulator back (warp w owns TMEM lanes 32 (w % 4) ..), subtract it from each C
+//    box in shared memory as the box arrives, and store the box with TMA; a slot is handed back to the
+//    C loader once the store of the box after it has been issued and its own store has read the slot.
+// The tile's update is HBM-bound (its C tile is read and written once per step; the panels stay in L2),
+// so the point is to keep loads and stores in flight on every SM at all times.  A wait that times out
+// raises the CTA's abort flag, which ends every role's loop; the roles then wait (bounded) for their own
+// copies and MMAs in flight before the TMEM is freed.
+constexpr int NCS = 6;           // C box slots (16 KB each)
 struct __align__(1024) TcpSmem {
-  float c[4][TT][KCH];           // C tile (one buffer, 64 KB)
+  float c[NCS][TT][KCH];         // ring of C boxes (96 KB)
   float a_hi[NST][TT][KCH];
   float a_lo[NST][TT][KCH];
   float b_hi[NST][TT][KCH];
   float b_lo[NST][TT][KCH];
-  unsigned long long full[NST], empty[NST], c_full, c_empty, acc_full[2], acc_empty[2];
+  unsigned long long full[NST], empty[NST], c_full[NCS], c_empty[NCS], acc_full[2], acc_empty[2], drain;
   uint32_t tmem;
   volatile int abort;
 };
+static_assert(sizeof(TcpSmem) + 1024 <= 232448, "shared memory of the persistent update");
 
 __device__ __forceinline__ bool wait_or_abort(unsigned long long* bar, uint32_t parity, volatile int* abort) {
   if (mbar_try(bar, parity)) return true;
@@ -280,6 +288,18 @@ __device__ __forceinline__ bool wait_or_abort(unsigned long long* bar, uint32_t 
     }
   }
   return true;
+}
+
+// barrier over the 128 epilogue threads that also ORs a predicate across them: every thread gets the same
+// answer, so the epilogue warps always leave their loop together
+__device__ __forceinline__ bool epi_any(bool q) {
+  uint32_t r;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.u32 q, %1, 0;\n bar.red.or.pred p, 1, 128, q;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(r)
+      : "r"((uint32_t)q)
+      : "memory");
+  return r != 0;
 }
 
 __device__ __forceinline__ void tile_of(long long w, int k, int cnt, const int* __restrict__ order,
@@ -297,7 +317,7 @@ __device__ __forceinline__ void tile_of(long long w, int k, int cnt, const int* 
   rowB = (int)(ioff[b] + j0);
 }
 
-__global__ void __launch_bounds__(192, 1) k_gj_update_tcp(int k, int cnt, long long ntiles,
+__global__ void __launch_bounds__(224, 1) k_gj_update_tcp(int k, int cnt, long long ntiles,
                                                           const int* __restrict__ order,
                                                           const long long* __restrict__ pre2,
                                                           const int* __restrict__ bn,
@@ -316,12 +336,15 @@ __global__ void __launch_bounds__(192, 1) k_gj_update_tcp(int k, int cnt, long l
       mbar_init(&S.full[st], 1);
       mbar_init(&S.empty[st], 1);
     }
-    mbar_init(&S.c_full, 1);
-    mbar_init(&S.c_empty, 1);
+    for (int sl = 0; sl < NCS; ++sl) {
+      mbar_init(&S.c_full[sl], 1);
+      mbar_init(&S.c_empty[sl], 1);
+    }
     for (int q = 0; q < 2; ++q) {
       mbar_init(&S.acc_full[q], 1);
       mbar_init(&S.acc_empty[q], 128);
     }
+    mbar_init(&S.drain, 1);
     S.abort = 0;
     fence_mbar_init();
   }
@@ -333,13 +356,12 @@ __global__ void __launch_bounds__(192, 1) k_gj_update_tcp(int k, int cnt, long l
 
   if (warp == 0) {
     if (lane == 0) {
-      // producer
+      // operand producer
       long long q = 0;
-      int it = 0;
-      for (long long w = blockIdx.x; w < ntiles && !S.abort; w += gridDim.x, ++it) {
+      for (long long w = blockIdx.x; w < ntiles && !S.abort; w += gridDim.x) {
         int b, i0, j0, rowA, rowB;
         tile_of(w, k, cnt, order, pre2, bn, ioff, b, i0, j0, rowA, rowB);
-        for (int c = 0; c < TT / KCH; ++c, ++q) {
+        for (int c = 0; c < TT / KCH; ++c) {
           const int st = (int)(q % NST);
           if (q >= NST && !wait_or_abort(&S.empty[st], (uint32_t)(((q - NST) / NST) & 1), &S.abort)) break;
           mbar_expect_tx(&S.full[st], 4u * TT * KCH * 4u);
@@ -347,18 +369,38 @@ __global__ void __launch_bounds__(192, 1) k_gj_update_tcp(int k, int cnt, long l
           tma_load_2d(&S.a_lo[st][0][0], &pa_lo, c * KCH, rowA, &S.full[st]);
           tma_load_2d(&S.b_hi[st][0][0], &pb_hi, c * KCH, rowB, &S.full[st]);
           tma_load_2d(&S.b_lo[st][0][0], &pb_lo, c * KCH, rowB, &S.full[st]);
+          ++q;
         }
-        if (S.abort) break;
-        if (it > 0 && !wait_or_abort(&S.c_empty, (uint32_t)((it - 1) & 1), &S.abort)) break;
-        mbar_expect_tx(&S.c_full, (uint32_t)sizeof(S.c));
-        for (int qq = 0; qq < 4; ++qq) tma_load_2d(&S.c[qq][0][0], mat_maps + b, j0 + qq * KCH, i0, &S.c_full);
       }
+      if (S.abort)   // the chunks still in flight land before the CTA ends (the latest phase of each stage)
+        for (long long qq = q > NST ? q - NST : 0; qq < q; ++qq)
+          mbar_wait(&S.full[qq % NST], (uint32_t)((qq / NST) & 1));
+    }
+  } else if (warp == 6) {
+    if (lane == 0) {
+      // C producer: box g of the CTA = box g % 4 of its tile g / 4, in slot g % NCS
+      long long g = 0;
+      for (long long w = blockIdx.x; w < ntiles && !S.abort; w += gridDim.x) {
+        int b, i0, j0, rowA, rowB;
+        tile_of(w, k, cnt, order, pre2, bn, ioff, b, i0, j0, rowA, rowB);
+        for (int qq = 0; qq < 4; ++qq) {
+          const int sl = (int)(g % NCS);
+          if (g >= NCS && !wait_or_abort(&S.c_empty[sl], (uint32_t)(((g - NCS) / NCS) & 1), &S.abort)) break;
+          mbar_expect_tx(&S.c_full[sl], (uint32_t)(TT * KCH * sizeof(float)));
+          tma_load_2d(&S.c[sl][0][0], mat_maps + b, j0 + qq * KCH, i0, &S.c_full[sl]);
+          ++g;
+        }
+      }
+      if (S.abort)
+        for (long long gg = g > NCS ? g - NCS : 0; gg < g; ++gg)
+          mbar_wait(&S.c_full[gg % NCS], (uint32_t)((gg / NCS) & 1));
     }
   } else if (warp == 1) {
     if (lane == 0) {
       // MMA issuer
       long long q = 0;
       int it = 0;
+      bool issued = false;
       for (long long w = blockIdx.x; w < ntiles && !S.abort; w += gridDim.x, ++it) {
         const int ab = it & 1;
         if (it >= 2 && !wait_or_abort(&S.acc_empty[ab], (uint32_t)(((it - 2) >> 1) & 1), &S.abort)) break;
@@ -381,33 +423,48 @@ __global__ void __launch_bounds__(192, 1) k_gj_update_tcp(int k, int cnt, long l
             mma_tf32(acc, ah, bl, IDESC_TF32, 1);
             mma_tf32(acc, al, bh, IDESC_TF32, 1);
           }
+          issued = true;
           mma_commit(&S.empty[st]);
         }
         if (!ok) break;
         mma_commit(&S.acc_full[ab]);
+      }
+      if (S.abort && issued) {   // every MMA this thread issued has finished before the TMEM is freed
+        mma_commit(&S.drain);
+        mbar_wait(&S.drain, 0);
       }
     }
   } else {
     // epilogue: warps 2..5, TMEM lane quarter warp % 4
     const int quarter = warp & 3;
     const int r = quarter * 32 + lane;
+    const bool leader = warp == 2 && lane == 0;
+    long long g = 0;
     int it = 0;
-    for (long long w = blockIdx.x; w < ntiles; w += gridDim.x, ++it) {
+    bool stop = false;
+    for (long long w = blockIdx.x; w < ntiles && !stop; w += gridDim.x, ++it) {
       int b, i0, j0, rowA, rowB;
       tile_of(w, k, cnt, order, pre2, bn, ioff, b, i0, j0, rowA, rowB);
       const int ab = it & 1;
-      const bool ok = wait_or_abort(&S.acc_full[ab], (uint32_t)((it >> 1) & 1), &S.abort) &&
-                      wait_or_abort(&S.c_full, (uint32_t)(it & 1), &S.abort);
-      // all 128 epilogue threads take the same branch: a timeout anywhere sets the abort flag first
-      asm volatile("bar.sync 1, 128;\n" ::: "memory");
-      if (!ok || S.abort) break;
+      const bool ok = wait_or_abort(&S.acc_full[ab], (uint32_t)((it >> 1) & 1), &S.abort);
+      if (epi_any(!ok || S.abort)) break;
       tc_fence_after();
       const uint32_t acc = tmem + (uint32_t)(ab * TT) + ((uint32_t)(quarter * 32) << 16);
 #pragma unroll 1
-      for (int qq = 0; qq < 4; ++qq) {
+      for (int qq = 0; qq < 4; ++qq, ++g) {
+        const int sl = (int)(g % NCS);
         float v[32];
         tmem_ld32(acc + (uint32_t)(qq * KCH), v);
-        float* crow = &S.c[qq][r][0];
+        if (qq == 3) {   // the accumulator is read out: the MMAs of the tile after next may use it
+          tc_fence_before();
+          asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(&S.acc_empty[ab])) : "memory");
+        }
+        const bool okc = wait_or_abort(&S.c_full[sl], (uint32_t)((g / NCS) & 1), &S.abort);
+        if (epi_any(!okc || S.abort)) {
+          stop = true;
+          break;
+        }
+        float* crow = &S.c[sl][r][0];
 #pragma unroll
         for (int ch = 0; ch < 8; ++ch) {
           float4* p = reinterpret_cast<float4*>(crow + ((ch ^ (r & 7)) * 4));
@@ -418,19 +475,20 @@ __global__ void __launch_bounds__(192, 1) k_gj_update_tcp(int k, int cnt, long l
           x.w -= v[ch * 4 + 3];
           *p = x;
         }
-      }
-      tc_fence_before();
-      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(&S.acc_empty[ab])) : "memory");
-      fence_async_smem();
-      asm volatile("bar.sync 1, 128;\n" ::: "memory");
-      if (warp == 2 && lane == 0) {
-        for (int qq = 0; qq < 4; ++qq) tma_store_2d(mat_maps + b, j0 + qq * KCH, i0, &S.c[qq][0][0]);
-        asm volatile("cp.async.bulk.commit_group;\n" ::: "memory");
-        asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory");
-        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(&S.c_empty)) : "memory");
+        fence_async_smem();
+        asm volatile("bar.sync 1, 128;\n" ::: "memory");
+        if (leader) {
+          tma_store_2d(mat_maps + b, j0 + qq * KCH, i0, &S.c[sl][0][0]);
+          asm volatile("cp.async.bulk.commit_group;\n" ::: "memory");
+          // every store but the newest has read its slot: hand the previous box's slot back
+          asm volatile("cp.async.bulk.wait_group.read 1;\n" ::: "memory");
+          if (g > 0)
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(&S.c_empty[(g - 1) % NCS]))
+                         : "memory");
+        }
       }
     }
-    if (warp == 2 && lane == 0) asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory");
+    if (leader) asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory");
   }
   tc_fence_before();
   __syncthreads();
@@ -544,7 +602,7 @@ cudaError_t GjTc::step(const BlockSet& B, float* mat, int k, int cnt, const int*
   if (ntiles > 0 && I.persistent) {
     pns::count_launch();
     const unsigned grid = (unsigned)std::min<long long>(ntiles, I.sms);
-    k_gj_update_tcp<<<grid, 192, sizeof(TcpSmem) + 1024, s>>>(k, cnt, ntiles, d_order, d_pre2, B.d_n.as<int>(),
+    k_gj_update_tcp<<<grid, 224, sizeof(TcpSmem) + 1024, s>>>(k, cnt, ntiles, d_order, d_pre2, B.d_n.as<int>(),
                                                                B.d_ioff.as<long long>(), I.d_maps, I.pa_hi, I.pa_lo,
                                                                I.pb_hi, I.pb_lo, d_bad);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;

@@ -287,19 +287,33 @@ int build_coarse_t(Ctx& C, Precond& pc, int* d_bad) {
                         d_roff.as<long long>(), d_kc.as<int>(), rhs.as<double>()));
   {
     // closure blocks Abar = A_b on p_i plus the row sums of its couplings to f faces and other
-    // primary grids (Eqs. 6, 9): solved by the Woodbury identity on the primary-block inverses,
-    // then two steps of iterative refinement with FP64 residuals of Abar
+    // primary grids (Eqs. 6, 9): solved by the Woodbury identity on the primary-block inverses (the
+    // capacitance inverses in the same precision), then iterative refinement with FP64 residuals of Abar:
+    // at least two steps, more while the residual norm still falls by 2x per step and is above 1e-14 of
+    // the right-hand side's (at most six)
     Woodbury WB;
     CK(WB.setup<SB>(C, B, pc.op, pc.state.as<double>(), B.mat.as<SB>(), kc, d_bad));
-    DevBuf Y, res, ds;
+    DevBuf Y, res, ds, dn;
     CK(dalloc(Y, sizeof(double) * std::max(1LL, rtot)));
     CK(dalloc(res, sizeof(double) * std::max(1LL, rtot)));
     CK(dalloc(ds, sizeof(double) * std::max(1LL, rtot)));
+    CK(dalloc(dn, sizeof(double) * (1 + 1024)));   // the norm, then the dot product's block partials
     CK(WB.apply<SB>(C, B, B.mat.as<SB>(), rhs.as<double>(), out.as<double>(), Y.as<double>(),
                     d_roff.as<long long>(), d_kc.as<int>(), kc));
-    for (int it = 0; it < 2; ++it) {
+    auto sq_norm = [&](const double* v, double& out_v) -> cudaError_t {
+      cudaError_t e2 = launch_dot(v, v, rtot, dn.as<double>() + 1, dn.as<double>(), s);
+      if (e2 != cudaSuccess) return e2;
+      return cudaMemcpy(&out_v, dn.p, sizeof(double), cudaMemcpyDeviceToHost);
+    };
+    double rhs2 = 0, prev2 = -1;
+    CK(sq_norm(rhs.as<double>(), rhs2));
+    for (int it = 0; it < 6; ++it) {
       CK(launch_closure_residual(C, B, pc.op, pc.state.as<double>(), d_roff.as<long long>(), d_kc.as<int>(),
                                  rhs.as<double>(), out.as<double>(), res.as<double>()));
+      double r2 = 0;
+      CK(sq_norm(res.as<double>(), r2));
+      if (it >= 2 && (r2 <= 1e-28 * rhs2 || (prev2 >= 0 && r2 > 0.25 * prev2))) break;
+      prev2 = r2;
       CK(WB.apply<SB>(C, B, B.mat.as<SB>(), res.as<double>(), ds.as<double>(), Y.as<double>(),
                       d_roff.as<long long>(), d_kc.as<int>(), kc));
       CK(launch_add_vec(out.as<double>(), ds.as<double>(), rtot, s));
