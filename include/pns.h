@@ -112,6 +112,11 @@ typedef struct pns_options {
                               overlapped;
                             3 the same tensor-core product with one CTA per tile and no overlap.
                             Measured on a GB300, 96^3 sphere pack: 39.8 (0) and 80.1 (3) TFLOP/s */
+  int rebuild_every;     /* transient runs (pns_newton_solve with x_prev != NULL): 0 (default) keeps the
+                            preconditioner built once and reuses it at every time step (Sec. 8.2); k > 0
+                            rebuilds it at the initial guess of a time step once k time steps have been
+                            solved with the current one.  An aPLMM_S preconditioner does not depend on the
+                            state and is never rebuilt. */
 } pns_options;
 
 typedef struct pns_stats {
@@ -137,6 +142,7 @@ typedef struct pns_stats {
                                      vectors), assembly of A^o, inversion of A^o */
   double gj_update_bytes;         /* algorithmic bytes of the timed update launches: the trailing matrix read and
                                      written and the two panels read, FP32, per block and step (cumulative) */
+  long long precond_builds;       /* preconditioner builds of this context so far (cumulative) */
 } pns_stats;
 
 typedef struct pns_info {

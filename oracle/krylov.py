@@ -70,9 +70,10 @@ class Problem:
     """Geometry + parameters + maps of one solve."""
 
     def __init__(self, mask, labels, prm: mac.Params, periodic=(True, False, False), n_dilate=1, n_tag=1,
-                 iface_mode="pair"):
+                 iface_mode="pair", rowsum="all"):
         self.g = mac.Grid(mask, periodic)
         self.prm = prm
+        self.rowsum = rowsum
         self.pins = mac.pressure_pins(self.g)
         self.maps = build_maps(self.g, labels, self.pins, n_dilate, n_tag, iface_mode)
         self.r0 = mac.reference_norm(self.g, prm, self.pins)
@@ -95,7 +96,7 @@ class Problem:
 
     def preconditioner(self, variant, x_lin):
         A_b = self.build_matrix(variant, x_lin)
-        return Plmm(self.g, self.prm, self.maps, A_b, use_coarse=(variant != "ml_only")), A_b
+        return Plmm(self.g, self.prm, self.maps, A_b, use_coarse=(variant != "ml_only"), rowsum=self.rowsum), A_b
 
     def direct_step(self, x, x_prev=None):
         """Newton step with an exact sparse solve (for brute-force checks)."""
@@ -148,14 +149,21 @@ def stokes_solution(pb: Problem, tol=1e-12):
     return x
 
 
-def transient(pb: Problem, x_start, n_steps, variant="aplmm_ns", **kw):
-    """Backward Euler from x_start; the preconditioner is built once at x_start and reused
-    (factors reused across steps).  Returns (list of states, per-step stats)."""
+def transient(pb: Problem, x_start, n_steps, variant="aplmm_ns", rebuild_every=0, **kw):
+    """Backward Euler from x_start (Sec. 8.2).  The preconditioner is built at x_start and reused across
+    steps (factors reused); with rebuild_every = k > 0 it is rebuilt at the initial guess of every time
+    step that follows k steps solved with the current one (aPLMM_S, which does not depend on the state,
+    is never rebuilt).  Returns (list of states, per-step stats)."""
     assert pb.prm.transient
     M = pb.preconditioner(variant, x_start)
     xs = [np.array(x_start)]
     stats = []
+    since = 0
     for _ in range(n_steps):
+        if rebuild_every > 0 and since >= rebuild_every and variant != "aplmm_s":
+            M = pb.preconditioner(variant, xs[-1])
+            since = 0
+        since += 1
         x, st = newton(pb, xs[-1], variant=variant, x_prev=xs[-1], precond=M, **kw)
         xs.append(x)
         stats.append(st)

@@ -63,7 +63,7 @@ def closure_block(A_b, m, i):
 class Plmm:
     """Recipe form of the preconditioner, built once from the build matrix A_b."""
 
-    def __init__(self, g, prm, m, A_b, use_coarse=True):
+    def __init__(self, g, prm, m, A_b, use_coarse=True, rowsum="all"):
         self.g, self.m = g, m
         self.use_coarse = use_coarse
         self.n_ci = len(m.coarse_ifaces)
@@ -109,7 +109,8 @@ class Plmm:
             pval.append(np.ones(len(cells)))
         self.Phat = sp.csr_matrix((np.concatenate(pval), (np.concatenate(prow), np.concatenate(pcol))),
                                   shape=(g.nfull, self.n_o))
-        # restriction R^ (n_o x nfull): interface rows sum their cells, primary rows all unknowns of p_i
+        # restriction R^ (n_o x nfull): interface rows sum their cells; primary rows all unknowns of p_i
+        # (Eq. 18, the pattern of C^T), or with rowsum = "cells" only the cells (pressures) of p_i
         rrow, rcol = [], []
         for k, j in enumerate(m.coarse_ifaces):
             cells = g.pidx(m.iface_cells[j])
@@ -117,6 +118,8 @@ class Plmm:
             rcol.append(cells)
         for i in self.coarse_prim:
             Pi = m.prim_unknowns[i]
+            if rowsum == "cells":
+                Pi = Pi[Pi >= g.pidx(0)]
             rrow.append(np.full(len(Pi), self.coarse_of_prim[i]))
             rcol.append(Pi)
         rr = np.concatenate(rrow)

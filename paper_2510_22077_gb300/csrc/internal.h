@@ -137,6 +137,8 @@ struct Ctx {
   std::vector<cudaEvent_t> ev_pool;
   size_t ev_used = 0;
   double t_local_ms = 0;
+  long long n_builds = 0;        // preconditioner builds of this context (pns_stats.precond_builds)
+  int solves_since_build = 0;    // transient Newton solves with the context's preconditioner since its build
   long long local_launches = 0;
   const double* cur_state = nullptr;   // Newton state for COMBINE_CURRENT
   double t_setup_ms = 0;

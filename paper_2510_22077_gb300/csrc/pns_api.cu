@@ -591,6 +591,8 @@ int block_apply(Ctx& C, Precond& pc, const double* v, double* z) {
 
 int build_precond(Ctx& C, Precond& pc, int variant, const double* x_lin) {
   const cudaStream_t s = C.stream;
+  ++C.n_builds;
+  if (&pc == &C.pc) C.solves_since_build = 0;
   pc.built = false;
   pc.ns_residual_before = 0;
   pc.variant = variant;
@@ -900,6 +902,7 @@ int newton(Ctx& C, Precond& pc, int stokes, double* x, const double* x_prev, pns
   loc.t_gj_update_ms = C.gj.ms;
   loc.gj_update_flops = C.gj.flops;
   loc.gj_update_bytes = C.gj.bytes;
+  loc.precond_builds = C.n_builds;
   loc.gj_update_launches = C.gj.launches;
   loc.gj_update_tiles = C.gj.tiles;
   if (stt) *stt = loc;
@@ -950,6 +953,7 @@ void pns_default_options(pns_options* o) {
   o->block_inner_its = 20;
   o->block_inner_tol = 1e-2;
   o->gj_tensor_cores = 2;
+  o->rebuild_every = 0;
 }
 
 int pns_setup(pns_ctx** out, int nz, int ny, int nx, const uint8_t* mask, const int32_t* labels, double rho,
@@ -966,7 +970,7 @@ int pns_setup(pns_ctx** out, int nz, int ny, int nx, const uint8_t* mask, const 
   if (C.opt.restart < 1 || C.opt.restart > 127 || C.opt.n_dilate < 0 || C.opt.n_tag < 1 || C.opt.precision < 0 ||
       C.opt.precision > 2 || C.opt.variant < 0 || C.opt.variant > 4 || C.opt.block_inner_its < 1 ||
       C.opt.block_inner_its > 100 || !(C.opt.block_inner_tol > 0.0) || C.opt.gj_tensor_cores < 0 ||
-      C.opt.gj_tensor_cores > 3) {
+      C.opt.gj_tensor_cores > 3 || C.opt.rebuild_every < 0) {
     delete ctx;
     return PNS_ERR_ARG;
   }
@@ -1207,7 +1211,13 @@ int pns_autotune(pns_ctx* ctx, int* table, double* ms) {
 int pns_newton_solve(pns_ctx* ctx, double* x, const double* x_prev, pns_stats* st) {
   if (check_ctx(ctx) || !x) return PNS_ERR_ARG;
   Ctx& C = ctx->c;
-  if (!C.pc.built) CKS(build_precond(C, C.pc, C.opt.variant, x));
+  if (!C.pc.built) {
+    CKS(build_precond(C, C.pc, C.opt.variant, x));
+  } else if (x_prev && C.opt.rebuild_every > 0 && C.solves_since_build >= C.opt.rebuild_every &&
+             C.pc.variant != PNS_APLMM_S) {
+    CKS(build_precond(C, C.pc, C.opt.variant, x));   // at this time step's initial guess
+  }
+  if (x_prev) ++C.solves_since_build;
   return newton(C, C.pc, 0, x, x_prev, st);
 }
 

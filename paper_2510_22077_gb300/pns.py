@@ -38,7 +38,8 @@ class Options(ctypes.Structure):
                 ("restart", ctypes.c_int), ("max_fgmres", ctypes.c_int), ("max_newton", ctypes.c_int),
                 ("inner_tol", ctypes.c_double), ("newton_tol", ctypes.c_double), ("refine_steps", ctypes.c_int),
                 ("timing", ctypes.c_int), ("stream", ctypes.c_void_p), ("block_inner_its", ctypes.c_int),
-                ("block_inner_tol", ctypes.c_double), ("gj_tensor_cores", ctypes.c_int)]
+                ("block_inner_tol", ctypes.c_double), ("gj_tensor_cores", ctypes.c_int),
+                ("rebuild_every", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -50,7 +51,8 @@ class Stats(ctypes.Structure):
                 ("kernel_launches", ctypes.c_longlong), ("refine_residual_max", ctypes.c_double),
                 ("t_gj_update_ms", ctypes.c_double), ("gj_update_flops", ctypes.c_double),
                 ("gj_update_launches", ctypes.c_longlong), ("gj_update_tiles", ctypes.c_longlong),
-                ("t_mg_parts_ms", ctypes.c_double * 3), ("gj_update_bytes", ctypes.c_double)]
+                ("t_mg_parts_ms", ctypes.c_double * 3), ("gj_update_bytes", ctypes.c_double),
+                ("precond_builds", ctypes.c_longlong)]
 
     def as_dict(self):
         n = self.newton_its
@@ -62,7 +64,8 @@ class Stats(ctypes.Structure):
                 "kernel_launches": self.kernel_launches, "refine_residual_max": self.refine_residual_max,
                 "t_gj_update_ms": self.t_gj_update_ms, "gj_update_flops": self.gj_update_flops,
                 "gj_update_launches": self.gj_update_launches, "gj_update_tiles": self.gj_update_tiles,
-                "t_mg_parts_ms": list(self.t_mg_parts_ms), "gj_update_bytes": self.gj_update_bytes}
+                "t_mg_parts_ms": list(self.t_mg_parts_ms), "gj_update_bytes": self.gj_update_bytes,
+                "precond_builds": self.precond_builds}
 
 
 class Info(ctypes.Structure):
@@ -168,7 +171,7 @@ class Solver:
     def __init__(self, mask, labels, rho, mu, b, dt=0.0, variant="gplmm", precision="fp64", combine="build",
                  periodic=(True, False, False), n_dilate=1, n_tag=1, restart=100, max_fgmres=2000, max_newton=30,
                  inner_tol=1e-9, newton_tol=1e-8, timing=False, stream=None, block_inner_its=20,
-                 block_inner_tol=1e-2, refine_steps=-1, gj_tensor_cores=None):
+                 block_inner_tol=1e-2, refine_steps=-1, gj_tensor_cores=None, rebuild_every=0):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("libpns needs a CUDA device")
@@ -195,6 +198,7 @@ class Solver:
         o.refine_steps = int(refine_steps)
         if gj_tensor_cores is not None:
             o.gj_tensor_cores = int(gj_tensor_cores)
+        o.rebuild_every = int(rebuild_every)
         s = stream if stream is not None else torch.cuda.current_stream()
         o.stream = ctypes.c_void_p(s.cuda_stream)
         self.stream = s

@@ -40,3 +40,29 @@ def test_transient_steps_with_reused_preconditioner(c1_workload, oracle_levels, 
         its.append(st["fgmres_its"])
         x_prev = x
     S.close()
+
+
+def test_transient_rebuild_every_step(c1_workload):
+    """rebuild_every = 1: the library rebuilds the aPLMM_NS preconditioner at the initial guess of every
+    time step after the first (one build per step in pns_stats.precond_builds), as the oracle's driver does
+    with the same policy; every level matches the oracle's to 1e-8."""
+    from oracle import krylov
+    pb = problem(c1_workload, mu=MU, dt=DT)
+    xs, stats = krylov.transient(pb, np.zeros(pb.g.nfull), STEPS, variant="aplmm_ns", rebuild_every=1, tol=1e-11,
+                                 inner_tol=1e-12)
+    S = solver(c1_workload, mu=MU, dt=DT, variant="aplmm_ns", precision="fp64", newton_tol=1e-11, inner_tol=1e-12,
+               rebuild_every=1)
+    x_prev = S.zeros()
+    S.pns_build_precond(x_prev)
+    builds = []
+    for n in range(1, STEPS + 1):
+        x = x_prev.clone()
+        st = S.pns_newton_solve(x, x_prev)
+        builds.append(st["precond_builds"])
+        err = rel(x.cpu().numpy(), xs[n])
+        print(f"rebuild every step, step {n}: builds {st['precond_builds']} fgmres {st['fgmres_its']} "
+              f"(oracle {stats[n - 1]['fgmres_its']}) rel L2 {err:.2e}")
+        assert err < 1e-8, (n, err)
+        x_prev = x
+    assert builds == [1, 2, 3]
+    S.close()

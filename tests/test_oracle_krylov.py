@@ -127,3 +127,36 @@ def test_transient_driver_passes_the_previous_level():
         J = mac.restrict(g, pb.jacobian(x))
         x[g.unknown] += spla.spsolve(J.tocsc(), -r[g.unknown])
     assert np.linalg.norm(x - xs[2]) / np.linalg.norm(xs[2]) < 1e-11
+
+
+@pytest.mark.parametrize("variant,every,expect", [("aplmm_ns", 2, [0, 2, 4]), ("aplmm_ns", 1, [0, 1, 2, 3, 4]),
+                                                  ("aplmm_ns", 0, [0]), ("aplmm_s", 1, [0])])
+def test_transient_rebuild_policy(variant, every, expect):
+    """rebuild_every = k: the preconditioner is rebuilt at the initial guess of each time step that follows
+    k steps solved with the current one (the previous level, which is also the step's initial iterate);
+    0 keeps the start-up build; aPLMM_S (state-independent) is never rebuilt.  The states stay those of the
+    tridiagonal recurrence whatever the policy (Newton converges to the same level)."""
+    ny, nx = 6, 8
+    pb = _split_channel(nx, ny)
+    builds = []
+    orig = pb.preconditioner
+
+    def counting(v, x_lin):
+        builds.append(np.array(x_lin))
+        return orig(v, x_lin)
+
+    pb.preconditioner = counting
+    xs, stats = krylov.transient(pb, np.zeros(pb.g.nfull), 5, variant=variant, rebuild_every=every, tol=1e-13,
+                                 inner_tol=1e-14)
+    assert len(builds) == len(expect)
+    for b, n in zip(builds, expect):
+        assert np.array_equal(b, xs[n]), n
+    prm = pb.prm
+    T = 2 * np.eye(ny) - np.eye(ny, k=1) - np.eye(ny, k=-1)
+    T[0, 0] = T[-1, -1] = 3.0
+    K = prm.rho / prm.dt * np.eye(ny) + prm.mu * T
+    u1d = np.zeros(ny)
+    for n in range(1, 6):
+        u1d = np.linalg.solve(K, prm.rho / prm.dt * u1d + prm.rho * prm.b[0])
+        ux = pb.g.split(xs[n])[0][0].reshape(ny, nx)
+        assert np.abs(ux - u1d[:, None]).max() < 1e-11 * np.abs(u1d).max(), n

@@ -254,3 +254,26 @@ def test_primary_grid_without_source_gets_no_coarse_unknown():
         v[unk] = np.random.default_rng(0).standard_normal(len(unk))
         zl = Mlit @ v[unk]
         assert np.linalg.norm(M.apply(v, A_b)[unk] - zl) / np.linalg.norm(zl) < 1e-11
+
+
+
+@pytest.mark.parametrize("kind,seed", [("tiny2d", 0), ("tiny3d", 1)])
+def test_cells_only_restriction_leaves_the_coarse_matrix_singular(kind, seed):
+    """Eq. 18 sums every unknown of p_i (the pattern of C^T).  Summing only its cells, the alternative
+    some readings allow, makes every coarse row a sum of continuity equations, which are linearly
+    dependent over a closed or periodic domain: A^o becomes singular, so that form is not offered by the
+    library."""
+    w = inputs.make_workload(kind, seed=seed)
+    conds = {}
+    for r in ("all", "cells"):
+        pb = krylov.Problem(w.mask, w.labels, mac.Params(1.0, 0.3, (1.0, 0.0, 0.0)), rowsum=r)
+        if pb.maps.n_iface == 0:
+            pytest.skip("fixture has no interface")
+        M, A_b = pb.preconditioner("gplmm", krylov.stokes_solution(pb))
+        sv = np.linalg.svd(M.Ao, compute_uv=False)
+        conds[r] = sv[0] / sv[-1]
+        if r == "cells":
+            prim_rows = M.Rhat[M.n_ci:].tocoo()
+            assert prim_rows.nnz > 0 and np.all(prim_rows.col >= pb.g.pidx(0))
+    assert conds["all"] < 1e6
+    assert conds["cells"] > 1e12
