@@ -186,7 +186,10 @@ int pns_get_info(const pns_ctx* ctx, pns_info* info);
  * layout) for backward Euler, or NULL (steady, or transient with u_prev = 0). */
 int pns_residual(pns_ctx* ctx, const double* x, const double* x_prev, double* r);
 
-/* y = J(x_lin) v: the Newton Jacobian at x_lin, upwind branches frozen at x_lin (FP64). */
+/* y = J(x_lin) v: the Newton Jacobian of the residual of Eq. 3 at x_lin, i.e. the matrix of the linear
+ * system FGMRES solves at each Newton step (Sec. 8, Eq. 3 differentiated), upwind branches frozen at
+ * x_lin (FP64, matrix-free).  x_lin, v, y: device, full layout; y may not alias v.  PNS_ERR_ARG for a
+ * NULL pointer. */
 int pns_jacobian_apply(pns_ctx* ctx, const double* x_lin, const double* v, double* y);
 
 /* y = A v for the build-matrix operator of a variant (enum pns_variant; ML_ONLY = GPLMM) at the
