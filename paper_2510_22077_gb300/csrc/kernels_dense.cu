@@ -233,7 +233,8 @@ __global__ void k_gj_rowpanel(int k, int cnt, const int* __restrict__ order, con
     }
 }
 
-// A[I, J] -= A[I, P] * A[P, J] for tiles I != k, J != k (FP64 path; FP32 uses k_mm128_gj_update)
+// A[I, J] -= A[I, P] * A[P, J] for tiles I != k, J != k (FP64 path; the FP32 path uses k_gj_update_tcp or,
+// with gj_tensor_cores 0 / 1, k_mm128_gj_update / k_mm128_gj_update_tc)
 template <typename ST, int TBK>
 __global__ void k_gj_update(int k, int cnt, const int* __restrict__ order, const long long* __restrict__ pre2,
                             const int* __restrict__ bn, const int* __restrict__ bld, const long long* __restrict__ moff,
