@@ -79,3 +79,35 @@ def test_product_path_fails_loudly_without_a_device(lib_path):
     rc = lib.pns_setup(ctypes.byref(ctx), 1, 4, 8, mask.ctypes.data_as(ctypes.c_void_p),
                        labels.ctypes.data_as(ctypes.c_void_p), 1.0, 1.0, b, 0.0, ctypes.byref(opt))
     assert rc != 0 and not ctx.value
+
+
+def test_binding_structs_match_the_header_layout(tmp_path):
+    """The ctypes mirrors of pns_options, pns_stats and pns_info have the C layout of include/pns.h: the same
+    size and every field at the same offset (a C program compiled against the header prints them)."""
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc not available")
+    from paper_2510_22077_gb300 import pns
+    structs = {"pns_options": pns.Options, "pns_stats": pns.Stats, "pns_info": pns.Info}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "pns.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'  printf("{cname} sizeof %zu\\n", sizeof({cname}));')
+        for f in py._fields_:
+            lines.append(f'  printf("{cname} {f[0]} %zu\\n", offsetof({cname}, {f[0]}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    r = subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], capture_output=True,
+                       text=True)
+    assert r.returncode == 0, r.stderr
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for cname, py in structs.items():
+        assert got[(cname, "sizeof")] == ctypes_sizeof(py), cname
+        for f in py._fields_:
+            assert got[(cname, f[0])] == getattr(py, f[0]).offset, (cname, f[0])
+
+
+def ctypes_sizeof(t):
+    import ctypes
+    return ctypes.sizeof(t)
