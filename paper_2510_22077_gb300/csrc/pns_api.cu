@@ -303,7 +303,8 @@ int build_coarse_t(Ctx& C, Precond& pc, int* d_bad) {
     auto sq_norm = [&](const double* v, double& out_v) -> cudaError_t {
       cudaError_t e2 = launch_dot(v, v, rtot, dn.as<double>() + 1, dn.as<double>(), s);
       if (e2 != cudaSuccess) return e2;
-      return cudaMemcpy(&out_v, dn.p, sizeof(double), cudaMemcpyDeviceToHost);
+      e2 = cudaMemcpyAsync(&out_v, dn.p, sizeof(double), cudaMemcpyDeviceToHost, s);
+      return e2 != cudaSuccess ? e2 : cudaStreamSynchronize(s);
     };
     double rhs2 = 0, prev2 = -1;
     CK(sq_norm(rhs.as<double>(), rhs2));
